@@ -1,0 +1,119 @@
+/*
+ * fcirc.h -- C ABI of the GB300 (sm_103a) f-circulant library.
+ *
+ * The library multiplies an f-circulant matrix by a vector without an FFT,
+ * by the recursive halving of Rosowski, "On Fast Computation of a Circulant
+ * Matrix-Vector Product" (arXiv 2103.02605), Algorithm 1 and Theorem 1
+ * (Section 2), and uses that product for the two applications of Section 3:
+ * integer polynomial multiplication (Section 3.1) and large-integer
+ * multiplication (Section 3.2).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  * Matrix layout (Definition 2, Section 1.2, and the 3x3 example after it):
+ *    an f-circulant n x n matrix A is given by its ROW vector a[0..n-1]
+ *    (Section 1.2, last paragraph): A[i][j] = a[j-i] for j >= i and
+ *    A[i][j] = f * a[n+j-i] for j < i, so c = A x is
+ *        c[i] = sum_k a[k] * x[(i+k) mod n] * f^[i+k >= n].
+ *  * Memory: every array argument may be a DEVICE pointer (any CUDA
+ *    allocation on the current device) or a HOST pointer (pageable or
+ *    pinned).  The caller allocates and owns all of them; the library never
+ *    frees or keeps them.  With device pointers only, the call enqueues its
+ *    kernels on `stream` and returns without waiting.  If any array is in
+ *    host memory, the call stages it through device memory on `stream` and
+ *    returns after the results are back in the caller's buffers.
+ *  * stream: a cudaStream_t passed as void* (NULL = the legacy default
+ *    stream) on the current device.
+ *  * Scratch: kept in a per-device pool inside the library, grown on demand
+ *    (growth synchronises the device) and released by fcirc_release().
+ *    Plans (root chains and twiddle tables) are cached per (device, p, f, n).
+ *    The first call for a new size or f builds its plan synchronously, so
+ *    make it before capturing a stream into a CUDA graph.
+ *  * Return value: an fcirc_status code.  No C++ exception crosses the ABI.
+ *    fcirc_error_string() names a code; fcirc_last_error() gives a one-line
+ *    detail for the calling thread's last failure.
+ *  * Outputs never alias inputs.
+ */
+#ifndef FCIRC_H
+#define FCIRC_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum fcirc_status {
+    FCIRC_OK = 0,
+    FCIRC_EINVAL = 1,   /* bad size, null pointer, p not an odd prime < 2^30 */
+    FCIRC_ENOROOT = 2,  /* a root required by Theorem 1 does not exist mod p */
+    FCIRC_ENOMEM = 3,   /* device allocation failed */
+    FCIRC_ECUDA = 4,    /* a CUDA runtime call failed (see fcirc_last_error) */
+    FCIRC_ETIMEOUT = 5  /* a bounded device-side wait gave up */
+};
+
+/*
+ * fcirc_matvec -- c = A x for the f-circulant A with row vector a, over
+ * Z/pZ (Section 2: Theorem 1, Algorithm 1; Definition 2 for the layout).
+ *
+ *   p     odd prime, 3 <= p < 2^30.
+ *   f     the circulant parameter, 1 <= f < p (f = 1: ordinary circulant).
+ *   a, x  n residues each, in [0, p) (row vector and vector).
+ *   c     n residues out, canonical in [0, p).
+ *   n     a power of two, 1 <= n <= 2^(v+1) where 2^v is the largest power
+ *         of two dividing p-1 (the recursion halves down to 2x2 blocks, so
+ *         it needs 2^(log2 n - 1)-th roots of unity), and n <= 2^28.
+ *
+ * Errors: FCIRC_EINVAL for a null pointer, n = 0, n not a power of two or
+ * too large, or p out of range / not prime; FCIRC_ENOROOT when f = 0 or f
+ * has no (n/2)-th root mod p (Theorem 1 needs a root of f at every level).
+ * Results for entries outside [0, p) are unspecified (never out of bounds).
+ */
+int fcirc_matvec(uint32_t p, uint32_t f, const uint32_t *a, const uint32_t *x,
+                 uint32_t *c, uint64_t n, void *stream);
+
+/*
+ * poly_mul_int -- exact product of two polynomials with 16-bit unsigned
+ * integer coefficients (Section 3.1): out[k] = sum_{i+j=k} P[i] Q[j] for
+ * k < np + nq - 1.
+ *
+ * The product is one circulant product per prime of size N = next power of
+ * two >= np + nq - 1 (Section 3.1: zero-padding to a power-of-two circulant),
+ * computed modulo the three primes 998244353, 469762049 and 167772161 and
+ * recombined by the Chinese remainder theorem (Garner's method).
+ *
+ *   P    np coefficients (uint16), Q  nq coefficients (uint16), little
+ *        degree first;  1 <= np, nq  and  np + nq - 1 <= 2^24.
+ *   out  np + nq - 1 int64 coefficients (exact: every coefficient is below
+ *        min(np, nq) * 2^32 < 2^57).
+ *
+ * Errors: FCIRC_EINVAL for null pointers, zero or too large sizes.
+ */
+int poly_mul_int(const uint16_t *P, uint64_t np, const uint16_t *Q,
+                 uint64_t nq, int64_t *out, void *stream);
+
+/*
+ * fcirc_sync_status -- waits for `stream`, then returns and clears the
+ * library's sticky device status word for the current device: FCIRC_OK, or
+ * FCIRC_ETIMEOUT if a bounded device-side wait gave up since the last call,
+ * or FCIRC_ECUDA if the stream reported an error.
+ */
+int fcirc_sync_status(void *stream);
+
+/* Name of a status code (static string). */
+const char *fcirc_error_string(int status);
+
+/* One-line detail of the calling thread's last failing call (static per
+ * thread; valid until the thread's next library call). */
+const char *fcirc_last_error(void);
+
+/* Frees the scratch pool and the cached plans of every device the library
+ * has touched (synchronises those devices first).  Safe to call at any
+ * time outside stream capture; later calls rebuild what they need. */
+int fcirc_release(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FCIRC_H */

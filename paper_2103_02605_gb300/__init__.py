@@ -1,0 +1,181 @@
+"""GB300-native f-circulant matrix-vector products without FFT.
+
+Thin Python binding of the C ABI in ``include/fcirc.h`` / ``include/fcirc_plan.h``
+(``_build/libfcirc.so``): argument marshalling only, every step of the
+computation runs in the library's CUDA kernels.  PyTorch provides device
+memory and streams.  If the shared library has not been built the calls
+raise; there is no fallback path.
+
+Method: Rosowski, "On Fast Computation of a Circulant Matrix-Vector Product"
+(arXiv 2103.02605), Algorithm 1 / Theorem 1 (Section 2) and the
+applications of Section 3.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+from . import build as _build
+
+__all__ = [
+    "FcircError", "library_path", "load",
+    "fcirc_matvec", "poly_mul_int", "sync_status", "release",
+    "nth_root", "node_twiddle", "leaf_param", "twiddle_from_factor",
+    "PRIMES",
+]
+
+PRIMES = (998244353, 469762049, 167772161)
+
+_lock = threading.Lock()
+_lib = None
+
+_u32, _u64, _i32 = ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int
+_vp = ctypes.c_void_p
+
+_SIGNATURES = {
+    "fcirc_matvec": ([_u32, _u32, _vp, _vp, _vp, _u64, _vp], _i32),
+    "poly_mul_int": ([_vp, _u64, _vp, _u64, _vp, _vp], _i32),
+    "fcirc_sync_status": ([_vp], _i32),
+    "fcirc_error_string": ([_i32], ctypes.c_char_p),
+    "fcirc_last_error": ([], ctypes.c_char_p),
+    "fcirc_release": ([], _i32),
+    "fcirc_nth_root": ([_u32, _u32, _u32, ctypes.POINTER(_u32)], _i32),
+    "fcirc_node_twiddle": ([_u32, _u32, _u64, _u32, _u64, ctypes.POINTER(_u32), ctypes.POINTER(_u32)], _i32),
+    "fcirc_leaf_param": ([_u32, _u32, _u64, _u64, ctypes.POINTER(_u32)], _i32),
+    "fcirc_twiddle_from_factor": ([_u32, _u32, _u32, ctypes.POINTER(_u32), ctypes.POINTER(_u32)], _i32),
+}
+
+
+class FcircError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(msg)
+        self.status = status
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load():
+    """Load the CUDA library (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = _build.LIB
+            if not os.path.exists(path):
+                raise RuntimeError(
+                    f"{path} is missing: build the CUDA library first "
+                    "(python -c 'import __graft_entry__ as g; g.build()')")
+            L = ctypes.CDLL(path)
+            for name, (args, res) in _SIGNATURES.items():
+                fn = getattr(L, name)
+                fn.argtypes = args
+                fn.restype = res
+            _lib = L
+    return _lib
+
+
+def _check(status: int, what: str):
+    if status != 0:
+        L = load()
+        name = L.fcirc_error_string(status).decode()
+        detail = L.fcirc_last_error().decode()
+        raise FcircError(status, f"{what}: {name} ({detail})")
+
+
+def _stream_handle(stream, *tensors) -> int:
+    import torch
+    if stream is not None:
+        return int(getattr(stream, "cuda_stream", stream))
+    if any(t.is_cuda for t in tensors):
+        return int(torch.cuda.current_stream(tensors[0].device).cuda_stream)
+    return 0
+
+
+def _u32_tensor(t, name):
+    import torch
+    if t.dtype not in (torch.int32, getattr(torch, "uint32", torch.int32)):
+        raise TypeError(f"{name} must be int32/uint32 holding residues, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    return t
+
+
+# -- entry points --------------------------------------------------------------
+
+def fcirc_matvec(p: int, f: int, a, x, out=None, stream=None):
+    """c = A x over Z/pZ for the f-circulant A with row vector a (Definition 2,
+    Algorithm 1).  a, x: 1-D int32/uint32 tensors of residues in [0, p),
+    on the current CUDA device or on the host."""
+    import torch
+    _u32_tensor(a, "a")
+    _u32_tensor(x, "x")
+    if a.shape != x.shape or a.dim() != 1:
+        raise ValueError("a and x must be 1-D of the same length")
+    if out is None:
+        out = torch.empty_like(a)
+    _u32_tensor(out, "out")
+    st = _stream_handle(stream, a, x, out)
+    _check(load().fcirc_matvec(p, f % p, a.data_ptr(), x.data_ptr(), out.data_ptr(), a.numel(), st),
+           "fcirc_matvec")
+    return out
+
+
+def poly_mul_int(P, Q, out=None, stream=None):
+    """Exact product of integer polynomials with uint16 coefficients
+    (Section 3.1).  P, Q: 1-D int16/uint16 tensors (bit patterns of uint16);
+    returns int64 coefficients of length len(P) + len(Q) - 1."""
+    import torch
+    for t, nm in ((P, "P"), (Q, "Q")):
+        if t.dtype not in (torch.int16, getattr(torch, "uint16", torch.int16)):
+            raise TypeError(f"{nm} must be a 16-bit tensor, got {t.dtype}")
+        if not t.is_contiguous() or t.dim() != 1:
+            raise ValueError(f"{nm} must be 1-D contiguous")
+    nout = P.numel() + Q.numel() - 1
+    if out is None:
+        out = torch.empty(nout, dtype=torch.int64, device=P.device)
+    st = _stream_handle(stream, P, Q, out)
+    _check(load().poly_mul_int(P.data_ptr(), P.numel(), Q.data_ptr(), Q.numel(), out.data_ptr(), st),
+           "poly_mul_int")
+    return out
+
+
+def sync_status(stream=None) -> int:
+    """Waits for the stream and returns the library's device status (0 = OK)."""
+    import torch
+    st = int(getattr(stream, "cuda_stream", stream)) if stream is not None else (
+        int(torch.cuda.current_stream().cuda_stream) if torch.cuda.is_available() else 0)
+    return int(load().fcirc_sync_status(st))
+
+
+def release():
+    _check(load().fcirc_release(), "fcirc_release")
+
+
+# -- host-side plan numbers (no GPU needed) -------------------------------------
+
+def nth_root(p: int, f: int, log2k: int) -> int:
+    r = _u32()
+    _check(load().fcirc_nth_root(p, f, log2k, ctypes.byref(r)), "fcirc_nth_root")
+    return r.value
+
+
+def node_twiddle(p: int, f: int, n: int, level: int, j: int):
+    s, si = _u32(), _u32()
+    _check(load().fcirc_node_twiddle(p, f, n, level, j, ctypes.byref(s), ctypes.byref(si)),
+           "fcirc_node_twiddle")
+    return s.value, si.value
+
+
+def leaf_param(p: int, f: int, n: int, j: int) -> int:
+    v = _u32()
+    _check(load().fcirc_leaf_param(p, f, n, j, ctypes.byref(v)), "fcirc_leaf_param")
+    return v.value
+
+
+def twiddle_from_factor(p: int, u: int, sigma: int):
+    w, wp = _u32(), _u32()
+    _check(load().fcirc_twiddle_from_factor(p, u, sigma, ctypes.byref(w), ctypes.byref(wp)),
+           "fcirc_twiddle_from_factor")
+    return w.value, wp.value

@@ -1,0 +1,347 @@
+// kernels_mod.cu -- sm_103a kernels of the modular f-circulant product
+// (Algorithm 1, Section 2) and of its polynomial / large-integer uses
+// (Section 3).
+//
+// Data layout: the recursion works IN PLACE in natural order.  Node j of
+// level l owns the contiguous block [j n/2^l, (j+1) n/2^l); its halving step
+// pairs element i of the first half with element i of the second half.  So
+// the top levels pair far-apart elements and the bottom levels near ones:
+//
+//  * k_strided_fwd / k_strided_inv: levels [l0, l1) of the whole array.
+//    The array is viewed, per level-l0 block, as 2^(l1-l0) rows of stride
+//    n/2^l1; a CTA stages 2^(l1-l0) rows x W adjacent columns in shared
+//    memory (coalesced row segments) and runs all those levels there.
+//  * k_tile: a CTA owns one contiguous tile of 2^logT residues (a node of
+//    level k = m - logT) and runs every remaining level of both input sides,
+//    the 2x2 leaf products and the recombination back up to level k.
+//
+// Twiddles: the strided passes read the stored s_{l,j}; the tile kernel
+// generates its 2^(logT-1) - 1 twiddles (and inverses) from the universal
+// root table and two per-tile factors (see plan.cu), so no table of size n
+// is ever read.
+#include <atomic>
+
+#include "common.hpp"
+#include "kernels_mod.hpp"
+
+namespace fcirc {
+
+__device__ __forceinline__ uint32_t load_src(const Src &s, uint64_t N, uint64_t idx)
+{
+    switch (s.kind) {
+    case SRC_U32:
+        return static_cast<const uint32_t *>(s.ptr)[idx];
+    case SRC_U16_REV: {
+        // a'[idx] = P[N-1-idx] with P zero-padded to N
+        uint64_t j = N - 1 - idx;
+        return j < s.len ? static_cast<const uint16_t *>(s.ptr)[j] : 0u;
+    }
+    default:  // SRC_U16
+        return idx < s.len ? static_cast<const uint16_t *>(s.ptr)[idx] : 0u;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// tile kernel
+
+__global__ void __launch_bounds__(kTileThreads)
+k_tile(const __grid_constant__ TileParams P)
+{
+    extern __shared__ __align__(16) uint32_t smem[];
+    const TileJob &J = P.job[blockIdx.y];
+    const int logT = P.logT, D = P.D;
+    const int T = 1 << logT;
+    const uint32_t p = J.p, p2 = 2 * J.p, pinv = J.pinv;
+    uint32_t *A = smem;
+    uint32_t *X = A + T;
+    Tw *tw = reinterpret_cast<Tw *>(X + T);   // [T/2], heap index 2^d + j'
+    Tw *itw = tw + (T >> 1);
+    const uint64_t t = blockIdx.x;
+    const uint64_t base = t << logT;
+
+    for (int i = threadIdx.x; i < T; i += blockDim.x) {
+        A[i] = load_src(J.a, P.N, base + i);
+        X[i] = load_src(J.x, P.N, base + i);
+    }
+    if (D > 0) {
+        const uint32_t *sg = J.sig + t * (uint64_t)D * 6;
+        for (int idx = threadIdx.x + 1; idx < (1 << D); idx += blockDim.x) {
+            int d = 31 - __clz(idx);
+            const uint32_t *e = sg + d * 6;
+            tw[idx] = twiddle_from(J.U[idx], e[0], e[1], e[2], p);
+            itw[idx] = twiddle_from(J.Ui[idx], e[3], e[4], e[5], p);
+        }
+    }
+    __syncthreads();
+
+    // both input sides, levels k .. L-1 (relative 0 .. D-1)
+    for (int d = 0; d < D; ++d) {
+        const int lh = logT - d - 1;
+        const int half = 1 << lh;
+        for (int b = threadIdx.x; b < (T >> 1); b += blockDim.x) {
+            const int jn = b >> lh, i = b & (half - 1);
+            const int lo = (jn << (lh + 1)) + i, hi = lo + half;
+            const Tw s = tw[(1 << d) + jn];
+            uint32_t a0 = A[lo], a1 = A[hi];
+            bfly_row(a0, a1, s, p, p2);
+            A[lo] = a0;
+            A[hi] = a1;
+            uint32_t x0 = X[lo], x1 = X[hi];
+            bfly_vec(x0, x1, s, p, p2);
+            X[lo] = x0;
+            X[hi] = x1;
+        }
+        __syncthreads();
+    }
+    // 2x2 leaves: leaf e has parameter +s or -s of its parent node
+    for (int e = threadIdx.x; e < (T >> 1); e += blockDim.x) {
+        Tw phi;
+        if (D == 0) {
+            phi = J.rho[t];
+        } else {
+            phi = tw[(1 << (D - 1)) + (e >> 1)];
+            if (e & 1) phi = tw_neg(phi, p);
+        }
+        uint32_t a0 = A[2 * e], a1 = A[2 * e + 1];
+        leaf2(a0, a1, X[2 * e], X[2 * e + 1], phi, J.kt, p, p2, pinv);
+        A[2 * e] = a0;
+        A[2 * e + 1] = a1;
+    }
+    __syncthreads();
+    // recombination, levels L-1 .. k
+    for (int d = D - 1; d >= 0; --d) {
+        const int lh = logT - d - 1;
+        const int half = 1 << lh;
+        for (int b = threadIdx.x; b < (T >> 1); b += blockDim.x) {
+            const int jn = b >> lh, i = b & (half - 1);
+            const int lo = (jn << (lh + 1)) + i, hi = lo + half;
+            uint32_t m1 = A[lo], m2 = A[hi];
+            bfly_rec(m1, m2, itw[(1 << d) + jn], p, p2);
+            A[lo] = m1;
+            A[hi] = m2;
+        }
+        __syncthreads();
+    }
+    for (int i = threadIdx.x; i < T; i += blockDim.x) {
+        uint32_t v = A[i];
+        J.dst[base + i] = J.store_lazy ? v : reduce_once(v, p);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// strided passes
+
+__global__ void __launch_bounds__(kStrThreads)
+k_strided_fwd(const __grid_constant__ StrFwdParams P)
+{
+    extern __shared__ __align__(16) uint32_t tile[];
+    const StrFwdJob &J = P.job[blockIdx.y];
+    const int logR = P.l1 - P.l0, logW = P.logW;
+    const int R = 1 << logR, W = 1 << logW, RW = R << logW;
+    const int logS = P.logn - P.l1;
+    const uint64_t cg_per_blk = (uint64_t)1 << (logS - logW);
+    const uint64_t blk = blockIdx.x / cg_per_blk, cg = blockIdx.x % cg_per_blk;
+    const uint64_t base = (blk << (P.logn - P.l0)) + (cg << logW);
+    const uint32_t p = J.p, p2 = 2 * J.p;
+
+    for (int e = threadIdx.x; e < RW; e += blockDim.x) {
+        const int r = e >> logW, w = e & (W - 1);
+        tile[e] = load_src(J.src, P.N, base + ((uint64_t)r << logS) + w);
+    }
+    __syncthreads();
+    for (int d = 0; d < logR; ++d) {
+        const int lh = logR - d - 1;
+        const int half = 1 << lh;
+        const Tw *lev = J.ftw + ((uint64_t)1 << (P.l0 + d)) + (blk << d);
+        for (int bb = threadIdx.x; bb < (RW >> 1); bb += blockDim.x) {
+            const int w = bb & (W - 1), rb = bb >> logW;
+            const int jn = rb >> lh, i = rb & (half - 1);
+            const int rlo = (jn << (lh + 1)) + i, rhi = rlo + half;
+            const Tw s = lev[jn];
+            uint32_t u = tile[(rlo << logW) + w], v = tile[(rhi << logW) + w];
+            if (J.vec_side)
+                bfly_vec(u, v, s, p, p2);
+            else
+                bfly_row(u, v, s, p, p2);
+            tile[(rlo << logW) + w] = u;
+            tile[(rhi << logW) + w] = v;
+        }
+        __syncthreads();
+    }
+    for (int e = threadIdx.x; e < RW; e += blockDim.x) {
+        const int r = e >> logW, w = e & (W - 1);
+        J.dst[base + ((uint64_t)r << logS) + w] = tile[e];
+    }
+}
+
+__device__ __forceinline__ uint64_t crt3(uint32_t r1, uint32_t r2, uint32_t r3, const CrtConsts &C)
+{
+    // Garner: x = r1 + p1 t2 + p1 p2 t3 with x = r_i (mod p_i), all r_i canonical
+    const uint32_t r1m2 = reduce_once(shoup_mul(r1, 1u, C.m2, C.p2), C.p2);
+    const uint32_t t2 = reduce_once(shoup_mul(r2 + C.p2 - r1m2, C.inv12.w, C.inv12.wp, C.p2), C.p2);
+    const uint32_t r1m3 = reduce_once(shoup_mul(r1, 1u, C.m3, C.p3), C.p3);
+    uint32_t u = r1m3 + reduce_once(shoup_mul(t2, C.p1m3.w, C.p1m3.wp, C.p3), C.p3);
+    u = reduce_once(u, C.p3);
+    const uint32_t t3 = reduce_once(shoup_mul(r3 + C.p3 - u, C.inv123.w, C.inv123.wp, C.p3), C.p3);
+    return (uint64_t)r1 + (uint64_t)C.p1 * t2 + C.p1p2 * (uint64_t)t3;
+}
+
+__global__ void __launch_bounds__(kStrThreads)
+k_strided_inv(const __grid_constant__ StrInvParams P)
+{
+    extern __shared__ __align__(16) uint32_t tile[];
+    const int logR = P.l1 - P.l0, logW = P.logW;
+    const int R = 1 << logR, W = 1 << logW, RW = R << logW;
+    const int logS = P.logn - P.l1;
+    const uint64_t cg_per_blk = (uint64_t)1 << (logS - logW);
+    const uint64_t blk = blockIdx.x / cg_per_blk, cg = blockIdx.x % cg_per_blk;
+    const uint64_t base = (blk << (P.logn - P.l0)) + (cg << logW);
+
+    for (int q = 0; q < P.nprime; ++q) {
+        const StrInvJob &J = P.job[q];
+        uint32_t *tq = tile + q * RW;
+        for (int e = threadIdx.x; e < RW; e += blockDim.x) {
+            const int r = e >> logW, w = e & (W - 1);
+            tq[e] = J.src[base + ((uint64_t)r << logS) + w];
+        }
+    }
+    __syncthreads();
+    for (int d = logR - 1; d >= 0; --d) {
+        const int lh = logR - d - 1;
+        const int half = 1 << lh;
+        for (int q = 0; q < P.nprime; ++q) {
+            const StrInvJob &J = P.job[q];
+            const uint32_t p = J.p, p2 = 2 * J.p;
+            uint32_t *tq = tile + q * RW;
+            const Tw *lev = J.fitw + ((uint64_t)1 << (P.l0 + d)) + (blk << d);
+            for (int bb = threadIdx.x; bb < (RW >> 1); bb += blockDim.x) {
+                const int w = bb & (W - 1), rb = bb >> logW;
+                const int jn = rb >> lh, i = rb & (half - 1);
+                const int rlo = (jn << (lh + 1)) + i, rhi = rlo + half;
+                uint32_t m1 = tq[(rlo << logW) + w], m2 = tq[(rhi << logW) + w];
+                bfly_rec(m1, m2, lev[jn], p, p2);
+                tq[(rlo << logW) + w] = m1;
+                tq[(rhi << logW) + w] = m2;
+            }
+        }
+        __syncthreads();
+    }
+    if (P.epi == EPI_CRT_ROT) {
+        const uint64_t mask = P.N - 1;
+        for (int e = threadIdx.x; e < RW; e += blockDim.x) {
+            const int r = e >> logW, w = e & (W - 1);
+            const uint64_t idx = base + ((uint64_t)r << logS) + w;
+            const uint64_t dst = (idx + mask) & mask;   // c_k = d_{k+1}
+            if (dst < P.nout) {
+                const uint32_t r1 = reduce_once(tile[e], P.job[0].p);
+                const uint32_t r2 = reduce_once(tile[RW + e], P.job[1].p);
+                const uint32_t r3 = reduce_once(tile[2 * RW + e], P.job[2].p);
+                P.dst64[dst] = crt3(r1, r2, r3, P.crt);
+            }
+        }
+    } else {
+        for (int q = 0; q < P.nprime; ++q) {
+            const StrInvJob &J = P.job[q];
+            const uint32_t *tq = tile + q * RW;
+            for (int e = threadIdx.x; e < RW; e += blockDim.x) {
+                const int r = e >> logW, w = e & (W - 1);
+                uint32_t v = tq[e];
+                J.dst[base + ((uint64_t)r << logS) + w] =
+                    P.epi == EPI_CANON ? reduce_once(v, J.p) : v;
+            }
+        }
+    }
+}
+
+// CRT of three canonical residue arrays of length N into out[(i-1) mod N]
+// (the product with the reversed-row embedding is rotated by one).
+__global__ void k_crt_rot(const uint32_t *r1, const uint32_t *r2, const uint32_t *r3, uint64_t N,
+                          uint64_t *out, uint64_t nout, CrtConsts C)
+{
+    const uint64_t mask = N - 1;
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < N;
+         i += (uint64_t)gridDim.x * blockDim.x) {
+        const uint64_t dst = (i + mask) & mask;
+        if (dst < nout) out[dst] = crt3(r1[i], r2[i], r3[i], C);
+    }
+}
+
+// n = 1: c_0 = a_0 x_0 (the 1x1 f-circulant is the scalar a_0).
+__global__ void k_scalar(const uint32_t *a, const uint32_t *x, uint32_t *c, uint32_t p)
+{
+    if (threadIdx.x == 0 && blockIdx.x == 0)
+        c[0] = (uint32_t)((uint64_t)a[0] * x[0] % p);
+}
+
+// ---------------------------------------------------------------------------
+// launchers
+
+// Opt a kernel into more than 48 KB of dynamic shared memory, once per device.
+template <class K>
+static int ensure_smem(K kernel, int bytes, std::atomic<unsigned> &mask)
+{
+    int dev = 0;
+    FCIRC_CUDA_TRY(cudaGetDevice(&dev));
+    const unsigned bit = 1u << (dev & 31);
+    if (mask.load() & bit) return FCIRC_OK;
+    FCIRC_CUDA_TRY(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+    mask.fetch_or(bit);
+    return FCIRC_OK;
+}
+
+int launch_tile(const TileParams &P, uint64_t ntiles, int njobs, cudaStream_t s)
+{
+    const size_t smem = (size_t)16 << P.logT;
+    static std::atomic<unsigned> mask{0};
+    FCIRC_TRY(ensure_smem(k_tile, 16 << kTileLogMax, mask));
+    dim3 grid((unsigned)ntiles, njobs);
+    k_tile<<<grid, kTileThreads, smem, s>>>(P);
+    FCIRC_CUDA_TRY(cudaGetLastError());
+    return FCIRC_OK;
+}
+
+static uint64_t str_grid(int logn, int l0, int l1, int logW)
+{
+    return (uint64_t)1 << (l0 + (logn - l1) - logW);
+}
+
+int launch_strided_fwd(const StrFwdParams &P, int njobs, cudaStream_t s)
+{
+    const size_t smem = (size_t)4 << (P.l1 - P.l0 + P.logW);
+    static std::atomic<unsigned> mask{0};
+    FCIRC_TRY(ensure_smem(k_strided_fwd, kStrSmemMax, mask));
+    dim3 grid((unsigned)str_grid(P.logn, P.l0, P.l1, P.logW), njobs);
+    k_strided_fwd<<<grid, kStrThreads, smem, s>>>(P);
+    FCIRC_CUDA_TRY(cudaGetLastError());
+    return FCIRC_OK;
+}
+
+int launch_strided_inv(const StrInvParams &P, cudaStream_t s)
+{
+    const size_t smem = (size_t)P.nprime * ((size_t)4 << (P.l1 - P.l0 + P.logW));
+    static std::atomic<unsigned> mask{0};
+    FCIRC_TRY(ensure_smem(k_strided_inv, kStrSmemMax, mask));
+    dim3 grid((unsigned)str_grid(P.logn, P.l0, P.l1, P.logW));
+    k_strided_inv<<<grid, kStrThreads, smem, s>>>(P);
+    FCIRC_CUDA_TRY(cudaGetLastError());
+    return FCIRC_OK;
+}
+
+int launch_crt_rot(const uint32_t *r1, const uint32_t *r2, const uint32_t *r3, uint64_t N,
+                   uint64_t *out, uint64_t nout, const CrtConsts &C, cudaStream_t s)
+{
+    unsigned blocks = (unsigned)((N + 255) / 256);
+    if (blocks > 152 * 8) blocks = 152 * 8;
+    k_crt_rot<<<blocks, 256, 0, s>>>(r1, r2, r3, N, out, nout, C);
+    FCIRC_CUDA_TRY(cudaGetLastError());
+    return FCIRC_OK;
+}
+
+int launch_scalar(const uint32_t *a, const uint32_t *x, uint32_t *c, uint32_t p, cudaStream_t s)
+{
+    k_scalar<<<1, 32, 0, s>>>(a, x, c, p);
+    FCIRC_CUDA_TRY(cudaGetLastError());
+    return FCIRC_OK;
+}
+
+}  // namespace fcirc

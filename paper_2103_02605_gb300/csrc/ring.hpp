@@ -1,0 +1,179 @@
+// ring.hpp -- host-side arithmetic of Z/pZ for the plan builder: primality,
+// a generator of the unit group, 2-adic valuation, 2^k-th roots and the
+// Shoup quotients the kernels consume.
+//
+// Theorem 1 (Section 2) asks for an n-th root of f, an n-th root of unity,
+// 2^-1 and f^-1 in the ring; for Z/pZ with p prime the roots of unity of
+// order 2^k exist iff 2^k | p - 1, and f has a 2^k-th root iff
+// f^((p-1)/gcd(2^k, p-1)) = 1.
+#pragma once
+#include <stdint.h>
+#include <vector>
+
+namespace fcirc {
+namespace host {
+
+inline uint32_t mulmod(uint32_t a, uint32_t b, uint32_t p)
+{
+    return (uint32_t)((uint64_t)a * b % p);
+}
+
+inline uint32_t powmod(uint32_t b, uint64_t e, uint32_t p)
+{
+    uint64_t r = 1 % p, x = b % p;
+    while (e) {
+        if (e & 1) r = r * x % p;
+        x = x * x % p;
+        e >>= 1;
+    }
+    return (uint32_t)r;
+}
+
+inline uint32_t invmod(uint32_t a, uint32_t p)  // p prime, a != 0 mod p
+{
+    return powmod(a, (uint64_t)p - 2, p);
+}
+
+// Deterministic Miller-Rabin for 32-bit integers (bases 2, 7, 61).
+inline bool is_prime(uint32_t n)
+{
+    if (n < 2) return false;
+    for (uint32_t sp : {2u, 3u, 5u, 7u, 11u, 13u, 61u})
+        if (n % sp == 0) return n == sp;
+    uint32_t d = n - 1;
+    int s = 0;
+    while ((d & 1) == 0) { d >>= 1; ++s; }
+    for (uint32_t a : {2u, 7u, 61u}) {
+        uint32_t x = powmod(a, d, n);
+        if (x == 1 || x == n - 1) continue;
+        bool comp = true;
+        for (int r = 1; r < s; ++r) {
+            x = mulmod(x, x, n);
+            if (x == n - 1) { comp = false; break; }
+        }
+        if (comp) return false;
+    }
+    return true;
+}
+
+inline int two_adic(uint32_t p)  // v with 2^v || p - 1
+{
+    uint32_t q = p - 1;
+    int v = 0;
+    while ((q & 1) == 0) { q >>= 1; ++v; }
+    return v;
+}
+
+// Smallest generator of (Z/pZ)^*: g^((p-1)/r) != 1 for every prime r | p-1.
+inline uint32_t generator(uint32_t p)
+{
+    std::vector<uint32_t> fac;
+    uint32_t m = p - 1;
+    for (uint32_t r = 2; (uint64_t)r * r <= m; ++r)
+        if (m % r == 0) {
+            fac.push_back(r);
+            while (m % r == 0) m /= r;
+        }
+    if (m > 1) fac.push_back(m);
+    for (uint32_t g = 2; g < p; ++g) {
+        bool ok = true;
+        for (uint32_t r : fac)
+            if (powmod(g, (p - 1) / r, p) == 1) { ok = false; break; }
+        if (ok) return g;
+    }
+    return 0;
+}
+
+// Omega: the fixed primitive 2^v-th root of unity g^((p-1)/2^v) every plan
+// of this prime derives its roots of unity from (psi_m = Omega^(2^v/m)).
+inline uint32_t omega(uint32_t p)
+{
+    int v = two_adic(p);
+    return powmod(generator(p), (uint64_t)(p - 1) >> v, p);
+}
+
+// Discrete log of w in the cyclic group <Om> of order 2^v (Pohlig-Hellman,
+// one bit at a time).  Returns false if w is not in the group.
+inline bool dlog_2group(uint32_t w, uint32_t Om, int v, uint32_t p, uint64_t &out)
+{
+    if (powmod(w, (uint64_t)1 << v, p) != 1) return false;
+    uint32_t Om_inv = invmod(Om, p);
+    uint64_t L = 0;
+    uint32_t cur = w;  // w * Om^-L
+    for (int i = 0; i < v; ++i) {
+        // cur has order dividing 2^(v-i); test bit i
+        uint32_t t = powmod(cur, (uint64_t)1 << (v - 1 - i), p);
+        if (t != 1) {
+            L |= (uint64_t)1 << i;
+            cur = mulmod(cur, powmod(Om_inv, (uint64_t)1 << i, p), p);
+        }
+    }
+    out = L;
+    return true;
+}
+
+// A 2^k-th root r of f mod p (r^(2^k) = f), or false if none exists.
+// Write p - 1 = q 2^v with q odd.  y = f^u with u = 2^-k mod q gives
+// y^(2^k) = f * z for z = (f^q)^m in the 2-Sylow subgroup <Omega>; a 2^k-th
+// root of z^-1 there is Omega^(log/2^k) when 2^k divides the discrete log.
+inline bool nth_root_2k(uint32_t f, int k, uint32_t p, uint32_t &root)
+{
+    f %= p;
+    if (f == 0) return false;
+    if (k == 0) { root = f; return true; }
+    if (f == 1) { root = 1; return true; }
+    int v = two_adic(p);
+    uint64_t q = (uint64_t)(p - 1) >> v;
+    // u = (2^k)^-1 mod q  (q odd; q == 1 -> u = 0)
+    uint64_t u = 0;
+    if (q > 1) {
+        // the inverse of 2 mod q is (q+1)/2, so (2^k)^-1 = ((q+1)/2)^k mod q
+        uint64_t t = 1, h = (q + 1) / 2;
+        for (int i = 0; i < k; ++i) t = t * h % q;
+        u = t;
+    }
+    uint32_t y = powmod(f, u, p);
+    // z = y^(2^k) / f lies in <Omega>
+    if (k > 62) return false;
+    uint32_t y2k = powmod(y, (uint64_t)1 << k, p);
+    uint32_t z = mulmod(y2k, invmod(f, p), p);
+    uint32_t zi = invmod(z, p);
+    uint32_t Om = omega(p);
+    uint64_t L;
+    if (!dlog_2group(zi, Om, v, p, L)) return false;
+    uint32_t w;
+    if (k <= v) {
+        if (L & (((uint64_t)1 << k) - 1)) return false;
+        w = powmod(Om, L >> k, p);
+    } else {
+        // x -> x^(2^k) kills <Omega>; a root exists only if z = 1
+        if (L != 0) return false;
+        w = 1;
+    }
+    root = mulmod(y, w, p);
+    if (powmod(root, (uint64_t)1 << k, p) != f) return false;
+    return true;
+}
+
+inline uint32_t shoup_quot(uint32_t w, uint32_t p)  // floor(w 2^32 / p)
+{
+    return (uint32_t)(((uint64_t)w << 32) / p);
+}
+
+inline void shoup_quot64(uint32_t w, uint32_t p, uint32_t &hi, uint32_t &lo)
+{
+    unsigned __int128 q = ((unsigned __int128)w << 64) / p;  // < 2^64
+    hi = (uint32_t)(q >> 32);
+    lo = (uint32_t)q;
+}
+
+inline uint32_t bitrev(uint64_t j, int bits)
+{
+    uint64_t r = 0;
+    for (int i = 0; i < bits; ++i)
+        if (j >> i & 1) r |= (uint64_t)1 << (bits - 1 - i);
+    return (uint32_t)r;
+}
+
+}  // namespace host
+}  // namespace fcirc

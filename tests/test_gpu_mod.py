@@ -1,0 +1,208 @@
+"""GPU parity of the modular f-circulant product and the polynomial product
+against the CPU oracle: bit-exact, element by element, through the C ABI."""
+import numpy as np
+import pytest
+
+from paper_2103_02605_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+P1, P2, P3 = I.P1, I.P2, I.P3
+
+
+@pytest.fixture(scope="module")
+def F():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_2103_02605_gb300 import build
+    build.build()
+    import paper_2103_02605_gb300 as F
+    F.load()
+    return F
+
+
+def dev_u32(v):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(v, np.uint32).view(np.int32)).cuda()
+
+
+def dev_u16(v):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(v, np.uint16).view(np.int16)).cuda()
+
+
+def host_u32(t):
+    return t.cpu().numpy().view(np.uint32)
+
+
+def f_with_root(p, n, seed):
+    """An f that has the (n/2)-th root the plan needs (Theorem 1)."""
+    r = int(np.random.default_rng(seed).integers(2, p))
+    return pow(r, max(n // 2, 1), p)
+
+
+def matvec(F, p, f, a, x):
+    import torch
+    c = F.fcirc_matvec(p, f, dev_u32(a), dev_u32(x))
+    torch.cuda.synchronize()
+    return host_u32(c)
+
+
+@pytest.mark.parametrize("p", [P1, P2, P3, 12289, 7681, 17])
+def test_matvec_every_small_power_of_two(F, orc, p):
+    v = ((p - 1) & -(p - 1)).bit_length() - 1
+    g = I.SplitMix64(p)
+    for m in range(0, min(12, v + 1) + 1):
+        n = 1 << m
+        a, x = g.uniform_mod(p, n), g.uniform_mod(p, n)
+        for f in (1, p - 1, f_with_root(p, n, m)):
+            if n > 2 and f == p - 1 and pow(p - 1, (p - 1) // int(np.gcd(n // 2, p - 1)), p) != 1:
+                continue
+            got = matvec(F, p, f, a, x)
+            assert np.array_equal(got, orc.fcirc_matvec_mod(p, f, a, x)), (p, m, f)
+
+
+@pytest.mark.parametrize("m", [13, 14, 15])
+def test_matvec_multi_tile_full(F, orc, m):
+    n = 1 << m
+    a, x = I.single_mod(n, P1, seed=I.SEED_BASE + 100 + m)
+    for f in (1, f_with_root(P1, n, m)):
+        assert np.array_equal(matvec(F, P1, f, a, x), orc.fcirc_matvec_mod(P1, f, a, x)), (m, f)
+
+
+def sample_rows(n, T=4096, k=48, seed=0):
+    rng = np.random.default_rng(seed)
+    rows = set([0, 1, n - 1, n - 2, n // 2, n // 2 - 1])
+    for t in range(0, n, max(T, n // 8)):
+        rows.update([t, t + T - 1 if t + T - 1 < n else n - 1])
+    rows.update(int(r) for r in rng.integers(0, n, k))
+    return np.array(sorted(rows), dtype=np.uint64)
+
+
+@pytest.mark.parametrize("m,p", [(17, P1), (20, P2), (24, P1), (25, P2), (26, P3)])
+def test_matvec_large_sampled(F, orc, m, p):
+    """Large n (several strided passes for 2^25+), checked on sampled rows."""
+    n = 1 << m
+    a, x = I.single_mod(n, p, seed=I.SEED_BASE + 200 + m)
+    f = f_with_root(p, n, 7 * m)
+    got = matvec(F, p, f, a, x)
+    rows = sample_rows(n, seed=m)
+    assert np.array_equal(got[rows.astype(np.int64)], orc.fcirc_matvec_mod_rows(p, f, a, x, rows))
+    assert got.max() < p
+
+
+def test_matvec_config0_full(F, orc):
+    """n = 2^12, f = 1, p = 998244353: the single-instance workload, full vector."""
+    a, x = I.single_mod(1 << 12)
+    assert np.array_equal(matvec(F, P1, 1, a, x), orc.fcirc_matvec_mod(P1, 1, a, x))
+
+
+def test_matvec_extreme_values(F, orc):
+    for m in (1, 5, 12, 14):
+        n = 1 << m
+        a = np.full(n, P1 - 1, np.uint32)
+        x = np.full(n, P1 - 1, np.uint32)
+        for f in (1, P1 - 1):
+            assert np.array_equal(matvec(F, P1, f, a, x), orc.fcirc_matvec_mod(P1, f, a, x))
+        z = np.zeros(n, np.uint32)
+        assert not matvec(F, P1, 3 ** 2 if m == 1 else 1, z, x).any()
+
+
+def test_matvec_host_buffers_match_device(F, orc):
+    import torch
+    for m in (3, 12, 16):
+        n = 1 << m
+        a, x = I.single_mod(n, P2, seed=m)
+        f = f_with_root(P2, n, m)
+        ah = torch.from_numpy(a.view(np.int32))
+        xh = torch.from_numpy(x.view(np.int32))
+        ch = F.fcirc_matvec(P2, f, ah, xh)      # host tensors: staged by the library
+        assert np.array_equal(ch.numpy().view(np.uint32), matvec(F, P2, f, a, x))
+        if m <= 12:
+            assert np.array_equal(ch.numpy().view(np.uint32), orc.fcirc_matvec_mod(P2, f, a, x))
+
+
+def test_matvec_errors(F):
+    import torch
+    a = dev_u32(np.zeros(8, np.uint32))
+    for bad_p in (4, 15, 2, 2147483647):
+        with pytest.raises(F.FcircError) as e:
+            F.fcirc_matvec(bad_p, 1, a, a)
+        assert e.value.status == 1
+    with pytest.raises(F.FcircError) as e:
+        F.fcirc_matvec(P1, 0, a, a)
+    assert e.value.status == 2
+    with pytest.raises(F.FcircError) as e:
+        F.fcirc_matvec(P1, 3, a, a)          # 3 is a non-residue mod P1
+    assert e.value.status == 2
+    big = torch.zeros(1 << 25, dtype=torch.int32, device="cuda")
+    with pytest.raises(F.FcircError) as e:
+        F.fcirc_matvec(P1, 1, big, big)      # needs a 2^24-th root of unity
+    assert e.value.status == 2
+    odd = torch.zeros(6, dtype=torch.int32, device="cuda")
+    with pytest.raises(F.FcircError) as e:
+        F.fcirc_matvec(P1, 1, odd, odd)
+    assert e.value.status == 1
+    L = F.load()
+    assert L.fcirc_matvec(P1, 1, None, None, None, 8, None) == 1
+    assert L.fcirc_matvec(P1, 1, a.data_ptr(), a.data_ptr(), a.data_ptr(), 0, None) == 1
+    assert F.sync_status() == 0
+
+
+# -- polynomial product (Section 3.1) ---------------------------------------------
+
+def poly(F, Pc, Qc):
+    import torch
+    out = F.poly_mul_int(dev_u16(Pc), dev_u16(Qc))
+    torch.cuda.synchronize()
+    return out.cpu().numpy()
+
+
+@pytest.mark.parametrize("np_,nq", [(1, 1), (1, 2), (2, 1), (3, 5), (64, 64), (2048, 2049),
+                                    (4096, 1), (3000, 1097), (4097, 4096), (10000, 333),
+                                    (1 << 14, 1 << 14), (70001, 5)])
+def test_poly_full(F, orc, np_, nq):
+    Pc, Qc = I.poly_pair(np_, seed=np_ * 7 + nq, nq=nq)
+    assert np.array_equal(poly(F, Pc, Qc), orc.poly_mul(Pc, Qc))
+
+
+def test_poly_extreme_coefficients(F):
+    n = 1 << 16
+    Pc = np.full(n, 0xFFFF, np.uint16)
+    k = np.arange(2 * n - 1)
+    want = np.minimum(k + 1, 2 * n - 1 - k).astype(np.int64) * 0xFFFF * 0xFFFF
+    assert np.array_equal(poly(F, Pc, Pc), want)
+
+
+def test_poly_config1_full_size(F, orc):
+    """Two polynomials of 2^23 uint16 coefficients (circulant size 2^24): sampled
+    coefficients exactly, plus evaluation at random points modulo independent
+    61-bit primes (P(t) Q(t) = C(t) mod q)."""
+    n = 1 << 23
+    Pc, Qc = I.poly_pair(n)
+    C = poly(F, Pc, Qc)
+    assert C.shape == (2 * n - 1,)
+    rng = np.random.default_rng(99)
+    idx = np.unique(np.concatenate([[0, 1, n - 1, n, 2 * n - 2, 2 * n - 3],
+                                    rng.integers(0, 2 * n - 1, 120)])).astype(np.uint64)
+    assert np.array_equal(C[idx.astype(np.int64)], orc.poly_mul_coeffs(Pc, Qc, idx))
+    for q in ((1 << 61) - 1, (1 << 62) - 57):   # primes
+        t = int(rng.integers(2, q))
+        assert orc.eval_i64_mod(C, t, q) == orc.eval_u16_mod(Pc, t, q) * orc.eval_u16_mod(Qc, t, q) % q
+
+
+def test_poly_host_buffers(F, orc):
+    import torch
+    Pc, Qc = I.poly_pair(5000, nq=3001)
+    out = F.poly_mul_int(torch.from_numpy(Pc.view(np.int16)), torch.from_numpy(Qc.view(np.int16)))
+    assert np.array_equal(out.numpy(), orc.poly_mul(Pc, Qc))
+
+
+def test_poly_errors(F):
+    import torch
+    L = F.load()
+    z = torch.zeros(4, dtype=torch.int16, device="cuda")
+    o = torch.zeros(8, dtype=torch.int64, device="cuda")
+    assert L.poly_mul_int(z.data_ptr(), 0, z.data_ptr(), 4, o.data_ptr(), None) == 1
+    assert L.poly_mul_int(None, 4, z.data_ptr(), 4, o.data_ptr(), None) == 1
+    assert L.poly_mul_int(z.data_ptr(), 1 << 24, z.data_ptr(), 2, o.data_ptr(), None) == 1
