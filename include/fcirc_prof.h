@@ -1,0 +1,41 @@
+/*
+ * fcirc_prof.h -- launch tracing of the f-circulant library.
+ *
+ * While tracing is on, every kernel the library launches is bracketed by two
+ * CUDA events recorded on the stream it is launched on, so per-kernel device
+ * time can be read back without a profiler.  The paper has no counterpart
+ * (its timings are wall-clock minima, Section 3.1); this is measurement
+ * plumbing for the kernels of the C ABI in fcirc.h.
+ *
+ * Events are recorded only between fcirc_prof_start() and fcirc_prof_stop();
+ * tracing must be off while a stream is captured into a CUDA graph.
+ */
+#ifndef FCIRC_PROF_H
+#define FCIRC_PROF_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Clears previous records and turns tracing on (all threads, all devices). */
+int fcirc_prof_start(void);
+
+/* Turns tracing off; records are kept until the next fcirc_prof_start(). */
+int fcirc_prof_stop(void);
+
+/* Waits for the recorded events and writes one line per kernel name,
+ *   "<name> <launches> <total_ms>\n",
+ * into buf (NUL-terminated, truncated to len bytes).  Returns FCIRC_OK or an
+ * fcirc_status code. */
+int fcirc_prof_report(char *buf, uint64_t len);
+
+/* Number of kernel launches recorded since fcirc_prof_start(). */
+uint64_t fcirc_prof_launches(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FCIRC_PROF_H */

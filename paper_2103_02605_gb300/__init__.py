@@ -22,6 +22,7 @@ __all__ = [
     "FcircError", "library_path", "load",
     "fcirc_matvec", "poly_mul_int", "sync_status", "release",
     "nth_root", "node_twiddle", "leaf_param", "twiddle_from_factor",
+    "prof_start", "prof_stop", "prof_report", "prof_launches",
     "PRIMES",
 ]
 
@@ -44,6 +45,10 @@ _SIGNATURES = {
     "fcirc_node_twiddle": ([_u32, _u32, _u64, _u32, _u64, ctypes.POINTER(_u32), ctypes.POINTER(_u32)], _i32),
     "fcirc_leaf_param": ([_u32, _u32, _u64, _u64, ctypes.POINTER(_u32)], _i32),
     "fcirc_twiddle_from_factor": ([_u32, _u32, _u32, ctypes.POINTER(_u32), ctypes.POINTER(_u32)], _i32),
+    "fcirc_prof_start": ([], _i32),
+    "fcirc_prof_stop": ([], _i32),
+    "fcirc_prof_report": ([ctypes.c_char_p, _u64], _i32),
+    "fcirc_prof_launches": ([], _u64),
 }
 
 
@@ -151,6 +156,31 @@ def sync_status(stream=None) -> int:
 
 def release():
     _check(load().fcirc_release(), "fcirc_release")
+
+
+# -- launch tracing (include/fcirc_prof.h) ---------------------------------------
+
+def prof_start():
+    _check(load().fcirc_prof_start(), "fcirc_prof_start")
+
+
+def prof_stop():
+    _check(load().fcirc_prof_stop(), "fcirc_prof_stop")
+
+
+def prof_report() -> dict:
+    """{kernel name: (launches, total device ms)} since prof_start()."""
+    buf = ctypes.create_string_buffer(1 << 16)
+    _check(load().fcirc_prof_report(buf, len(buf)), "fcirc_prof_report")
+    out = {}
+    for line in buf.value.decode().splitlines():
+        name, cnt, ms = line.split()
+        out[name] = (int(cnt), float(ms))
+    return out
+
+
+def prof_launches() -> int:
+    return int(load().fcirc_prof_launches())
 
 
 # -- host-side plan numbers (no GPU needed) -------------------------------------

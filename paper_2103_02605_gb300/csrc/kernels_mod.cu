@@ -23,6 +23,7 @@
 
 #include "common.hpp"
 #include "kernels_mod.hpp"
+#include "prof.hpp"
 
 namespace fcirc {
 
@@ -295,6 +296,7 @@ int launch_tile(const TileParams &P, uint64_t ntiles, int njobs, cudaStream_t s)
     static std::atomic<unsigned> mask{0};
     FCIRC_TRY(ensure_smem(k_tile, 16 << kTileLogMax, mask));
     dim3 grid((unsigned)ntiles, njobs);
+    ProfScope ps("k_tile", s);
     k_tile<<<grid, kTileThreads, smem, s>>>(P);
     FCIRC_CUDA_TRY(cudaGetLastError());
     return FCIRC_OK;
@@ -311,6 +313,7 @@ int launch_strided_fwd(const StrFwdParams &P, int njobs, cudaStream_t s)
     static std::atomic<unsigned> mask{0};
     FCIRC_TRY(ensure_smem(k_strided_fwd, kStrSmemMax, mask));
     dim3 grid((unsigned)str_grid(P.logn, P.l0, P.l1, P.logW), njobs);
+    ProfScope ps("k_strided_fwd", s);
     k_strided_fwd<<<grid, kStrThreads, smem, s>>>(P);
     FCIRC_CUDA_TRY(cudaGetLastError());
     return FCIRC_OK;
@@ -322,6 +325,7 @@ int launch_strided_inv(const StrInvParams &P, cudaStream_t s)
     static std::atomic<unsigned> mask{0};
     FCIRC_TRY(ensure_smem(k_strided_inv, kStrSmemMax, mask));
     dim3 grid((unsigned)str_grid(P.logn, P.l0, P.l1, P.logW));
+    ProfScope ps("k_strided_inv", s);
     k_strided_inv<<<grid, kStrThreads, smem, s>>>(P);
     FCIRC_CUDA_TRY(cudaGetLastError());
     return FCIRC_OK;
@@ -332,6 +336,7 @@ int launch_crt_rot(const uint32_t *r1, const uint32_t *r2, const uint32_t *r3, u
 {
     unsigned blocks = (unsigned)((N + 255) / 256);
     if (blocks > 152 * 8) blocks = 152 * 8;
+    ProfScope ps("k_crt_rot", s);
     k_crt_rot<<<blocks, 256, 0, s>>>(r1, r2, r3, N, out, nout, C);
     FCIRC_CUDA_TRY(cudaGetLastError());
     return FCIRC_OK;
@@ -339,6 +344,7 @@ int launch_crt_rot(const uint32_t *r1, const uint32_t *r2, const uint32_t *r3, u
 
 int launch_scalar(const uint32_t *a, const uint32_t *x, uint32_t *c, uint32_t p, cudaStream_t s)
 {
+    ProfScope ps("k_scalar", s);
     k_scalar<<<1, 32, 0, s>>>(a, x, c, p);
     FCIRC_CUDA_TRY(cudaGetLastError());
     return FCIRC_OK;
