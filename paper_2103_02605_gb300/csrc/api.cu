@@ -133,10 +133,99 @@ TileJob tile_job(const Plan *pl, Src a, Src x, uint32_t *dst, int lazy)
     J.Ui = pl->pt->d_Ui;
     J.p = pl->p;
     J.pinv = pl->pt->pinv;
-    J.kt = pl->kt;
     J.store_lazy = lazy;
     return J;
 }
+
+// Pass dispatch: the register-staged kernels where their shapes apply, the
+// generic shared-memory kernels otherwise.
+int run_tile(const TileParams &P, uint64_t ntiles, int njobs, cudaStream_t s)
+{
+    return fast_tile_ok(P.logT) ? launch_tile_fast(P, ntiles, njobs, s) : launch_tile(P, ntiles, njobs, s);
+}
+
+// One forward strided pass (pass index `pass` of the plans' shape) for
+// `njobs` (source, destination, plan) jobs; the register-staged kernel runs
+// `jobs_per_cta` of them in one CTA when its shape applies.
+struct FwdDesc {
+    Src src;
+    uint32_t *dst;
+    const Plan *pl;
+    int vec_side;
+    int half;
+};
+
+int run_fwd_pass(int pass, const FwdDesc *jd, int njobs, int jobs_per_cta, cudaStream_t s)
+{
+    const Plan &sh = *jd[0].pl;
+    const int l0 = sh.pass_l0[pass], l1 = sh.pass_l1[pass];
+    if (fast_col_ok(l1 - l0, sh.m - l1)) {
+        ColFwdParams P{};
+        for (int k = 0; k < njobs; ++k)
+            P.job[k] = ColFwdJob{jd[k].src, jd[k].dst, jd[k].pl->d_gtw + jd[k].pl->pass_goff[pass],
+                                 jd[k].pl->p, jd[k].vec_side, jd[k].half};
+        P.jobs_per_cta = jobs_per_cta;
+        P.N = (uint32_t)sh.n;
+        P.logn = sh.m;
+        P.l0 = l0;
+        P.l1 = l1;
+        for (int st = 0; st < 3; ++st) P.stage_off[st] = sh.stage_off[pass][st];
+        return launch_colfwd(P, njobs / jobs_per_cta, s);
+    }
+    StrFwdParams P{};
+    for (int k = 0; k < njobs; ++k)
+        P.job[k] = StrFwdJob{jd[k].src, jd[k].dst, jd[k].pl->d_ftw, jd[k].pl->p, jd[k].vec_side};
+    P.N = sh.n;
+    P.logn = sh.m;
+    P.l0 = l0;
+    P.l1 = l1;
+    P.logW = 2;
+    return launch_strided_fwd(P, njobs, s);
+}
+
+struct InvDesc {
+    const uint32_t *src;
+    uint32_t *dst;
+    const Plan *pl;
+};
+
+int run_inv_pass(int pass, const InvDesc *jd, int nprime, int epi, uint64_t *dst64, uint64_t nout,
+                 const CrtConsts *crt, cudaStream_t s)
+{
+    const Plan &sh = *jd[0].pl;
+    const int l0 = sh.pass_l0[pass], l1 = sh.pass_l1[pass];
+    if (fast_col_ok(l1 - l0, sh.m - l1)) {
+        ColInvParams P{};
+        for (int q = 0; q < nprime; ++q)
+            P.job[q] = ColInvJob{jd[q].src, jd[q].dst, jd[q].pl->d_gitw + jd[q].pl->pass_goff[pass], jd[q].pl->p};
+        P.nprime = nprime;
+        P.N = (uint32_t)sh.n;
+        P.logn = sh.m;
+        P.l0 = l0;
+        P.l1 = l1;
+        for (int st = 0; st < 3; ++st) P.stage_off[st] = sh.stage_off[pass][st];
+        P.epi = epi;
+        P.dst64 = dst64;
+        P.nout = nout;
+        if (crt) P.crt = *crt;
+        return launch_colinv(P, s);
+    }
+    StrInvParams P{};
+    for (int q = 0; q < nprime; ++q) P.job[q] = StrInvJob{jd[q].src, jd[q].dst, jd[q].pl->d_fitw, jd[q].pl->p};
+    P.nprime = nprime;
+    P.N = sh.n;
+    P.logn = sh.m;
+    P.l0 = l0;
+    P.l1 = l1;
+    P.logW = 2;
+    P.epi = epi;
+    P.dst64 = dst64;
+    P.nout = nout;
+    if (crt) P.crt = *crt;
+    return launch_strided_inv(P, s);
+}
+
+Src src_u32(const void *ptr, uint64_t n) { return Src{ptr, n, SRC_U32, 0, Tw{0, 0}}; }
 
 }  // namespace
 
@@ -161,58 +250,48 @@ static int poly_core(const uint16_t *P, uint64_t np, const uint16_t *Q, uint64_t
         A[q] = reinterpret_cast<uint32_t *>(scratch) + (size_t)q * N;
         X[q] = reinterpret_cast<uint32_t *>(scratch) + (size_t)(3 + q) * N;
     }
-    const Src srcP{P, np, SRC_U16_REV}, srcQ{Q, nq, SRC_U16};
+    // row vector: P reversed (a'[i] = P[N-1-i]) and scaled by 2^32 2^-L for
+    // the leaf; vector: Q; both zero-padded to N
+    Src srcP[3], srcQ{Q, nq, SRC_U16, 0, Tw{0, 0}};
+    for (int q = 0; q < 3; ++q) srcP[q] = Src{P, np, SRC_U16_REV, 1, pl[q]->kt};
     const Plan &p0 = *pl[0];
     if (p0.k == 0) {
         TileParams tp;
-        for (int q = 0; q < 3; ++q) tp.job[q] = tile_job(pl[q], srcP, srcQ, A[q], 0);
+        for (int q = 0; q < 3; ++q) tp.job[q] = tile_job(pl[q], srcP[q], srcQ, A[q], 0);
         tp.N = N;
         tp.logT = p0.logT;
         tp.D = p0.D;
-        FCIRC_TRY(launch_tile(tp, 1, 3, s));
+        FCIRC_TRY(run_tile(tp, 1, 3, s));
         return launch_crt_rot(A[0], A[1], A[2], N, out, nout, crt, s);
     }
     for (int i = 0; i < p0.npass; ++i) {
-        StrFwdParams fp;
+        FwdDesc jd[6];
+        // f = 1 gives s = 1 at level 0; with both inputs shorter than N/2 that
+        // level only copies (row vector zero below N/2, vector from N/2)
+        const int half = (np <= N / 2 && nq <= N / 2) ? 1 : 0;
         for (int q = 0; q < 3; ++q) {
-            Src sa = srcP, sx = srcQ;
-            if (i > 0) {
-                sa = Src{A[q], N, SRC_U32};
-                sx = Src{X[q], N, SRC_U32};
+            if (i == 0) {
+                jd[q] = FwdDesc{srcP[q], A[q], pl[q], 0, half};
+                jd[3 + q] = FwdDesc{srcQ, X[q], pl[q], 1, 2 * half};
+            } else {
+                jd[q] = FwdDesc{src_u32(A[q], N), A[q], pl[q], 0, 0};
+                jd[3 + q] = FwdDesc{src_u32(X[q], N), X[q], pl[q], 1, 0};
             }
-            fp.job[2 * q] = StrFwdJob{sa, A[q], pl[q]->d_ftw, kPrimes[q], 0};
-            fp.job[2 * q + 1] = StrFwdJob{sx, X[q], pl[q]->d_ftw, kPrimes[q], 1};
         }
-        fp.N = N;
-        fp.logn = p0.m;
-        fp.l0 = p0.pass_l0[i];
-        fp.l1 = p0.pass_l1[i];
-        fp.logW = 2;
-        FCIRC_TRY(launch_strided_fwd(fp, 6, s));
+        FCIRC_TRY(run_fwd_pass(i, jd, 6, 3, s));
     }
     {
         TileParams tp;
-        for (int q = 0; q < 3; ++q)
-            tp.job[q] = tile_job(pl[q], Src{A[q], N, SRC_U32}, Src{X[q], N, SRC_U32}, A[q], 1);
+        for (int q = 0; q < 3; ++q) tp.job[q] = tile_job(pl[q], src_u32(A[q], N), src_u32(X[q], N), A[q], 1);
         tp.N = N;
         tp.logT = p0.logT;
         tp.D = p0.D;
-        FCIRC_TRY(launch_tile(tp, (uint64_t)1 << p0.k, 3, s));
+        FCIRC_TRY(run_tile(tp, (uint64_t)1 << p0.k, 3, s));
     }
     for (int i = p0.npass - 1; i >= 0; --i) {
-        StrInvParams ip;
-        for (int q = 0; q < 3; ++q) ip.job[q] = StrInvJob{A[q], A[q], pl[q]->d_fitw, kPrimes[q]};
-        ip.nprime = 3;
-        ip.N = N;
-        ip.logn = p0.m;
-        ip.l0 = p0.pass_l0[i];
-        ip.l1 = p0.pass_l1[i];
-        ip.logW = 2;
-        ip.epi = (i == 0) ? EPI_CRT_ROT : EPI_LAZY;
-        ip.dst64 = out;
-        ip.nout = nout;
-        ip.crt = crt;
-        FCIRC_TRY(launch_strided_inv(ip, s));
+        InvDesc jd[3];
+        for (int q = 0; q < 3; ++q) jd[q] = InvDesc{A[q], A[q], pl[q]};
+        FCIRC_TRY(run_inv_pass(i, jd, 3, i == 0 ? EPI_CRT_ROT : EPI_LAZY, out, nout, &crt, s));
     }
     return FCIRC_OK;
 }
@@ -266,53 +345,34 @@ int fcirc_matvec(uint32_t p, uint32_t f, const uint32_t *a, const uint32_t *x, u
         FCIRC_TRY(launch_scalar(da, dx, dc, p, s));
         return st.end();
     }
+    // the row vector is scaled by 2^32 2^-L on its first load (see leaf2)
+    const Src sa{da, n, SRC_U32, 1, pl->kt}, sx = src_u32(dx, n);
     if (pl->k == 0) {
         TileParams tp;
-        tp.job[0] = tile_job(pl, Src{da, n, SRC_U32}, Src{dx, n, SRC_U32}, dc, 0);
+        tp.job[0] = tile_job(pl, sa, sx, dc, 0);
         tp.N = n;
         tp.logT = pl->logT;
         tp.D = pl->D;
-        FCIRC_TRY(launch_tile(tp, 1, 1, s));
+        FCIRC_TRY(run_tile(tp, 1, 1, s));
         return st.end();
     }
     uint32_t *xs = reinterpret_cast<uint32_t *>(st.scratch);
     for (int i = 0; i < pl->npass; ++i) {
-        StrFwdParams fp;
-        Src sa{da, n, SRC_U32}, sx{dx, n, SRC_U32};
-        if (i > 0) {
-            sa.ptr = dc;
-            sx.ptr = xs;
-        }
-        fp.job[0] = StrFwdJob{sa, dc, pl->d_ftw, p, 0};
-        fp.job[1] = StrFwdJob{sx, xs, pl->d_ftw, p, 1};
-        fp.N = n;
-        fp.logn = pl->m;
-        fp.l0 = pl->pass_l0[i];
-        fp.l1 = pl->pass_l1[i];
-        fp.logW = 2;
-        FCIRC_TRY(launch_strided_fwd(fp, 2, s));
+        FwdDesc jd[2] = {FwdDesc{i == 0 ? sa : src_u32(dc, n), dc, pl, 0, 0},
+                         FwdDesc{i == 0 ? sx : src_u32(xs, n), xs, pl, 1, 0}};
+        FCIRC_TRY(run_fwd_pass(i, jd, 2, 1, s));
     }
     {
         TileParams tp;
-        tp.job[0] = tile_job(pl, Src{dc, n, SRC_U32}, Src{xs, n, SRC_U32}, dc, 1);
+        tp.job[0] = tile_job(pl, src_u32(dc, n), src_u32(xs, n), dc, 1);
         tp.N = n;
         tp.logT = pl->logT;
         tp.D = pl->D;
-        FCIRC_TRY(launch_tile(tp, (uint64_t)1 << pl->k, 1, s));
+        FCIRC_TRY(run_tile(tp, (uint64_t)1 << pl->k, 1, s));
     }
     for (int i = pl->npass - 1; i >= 0; --i) {
-        StrInvParams ip;
-        ip.job[0] = StrInvJob{dc, dc, pl->d_fitw, p};
-        ip.nprime = 1;
-        ip.N = n;
-        ip.logn = pl->m;
-        ip.l0 = pl->pass_l0[i];
-        ip.l1 = pl->pass_l1[i];
-        ip.logW = 2;
-        ip.epi = (i == 0) ? EPI_CANON : EPI_LAZY;
-        ip.dst64 = nullptr;
-        ip.nout = 0;
-        FCIRC_TRY(launch_strided_inv(ip, s));
+        InvDesc jd[1] = {InvDesc{dc, dc, pl}};
+        FCIRC_TRY(run_inv_pass(i, jd, 1, i == 0 ? EPI_CANON : EPI_LAZY, nullptr, 0, nullptr, s));
     }
     return st.end();
 }

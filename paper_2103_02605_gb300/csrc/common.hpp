@@ -87,6 +87,11 @@ struct Plan {
     Tw *d_fitw = nullptr;           // [2^k] their inverses
     uint32_t *d_sig = nullptr;      // [2^k][D][6]: sigma, quotient hi, lo, and the same for sigma^-1
     Tw *d_rho = nullptr;            // [2^k] tile roots rho_t (used when D == 0)
+    // the same top-level twiddles in group order, per strided pass (see
+    // ColFwdJob in kernels_mod.hpp); offsets in entries
+    Tw *d_gtw = nullptr, *d_gitw = nullptr;
+    int pass_goff[4] = {0};
+    int stage_off[4][3] = {{0}};
 };
 
 int get_plan(uint32_t p, uint32_t f, uint64_t n, const Plan **out);

@@ -1,0 +1,686 @@
+// kernels_fast.cu -- register-staged sm_103a kernels for the large modular
+// path: the recursion of Algorithm 1 (Section 2) run as radix-16 register
+// stages with shared-memory transposes in between.
+//
+// A thread keeps 16 residues of each side in registers and runs up to four
+// halving levels on them without moving data (the 16 residues of a group are
+// exactly the elements a 4-level subtree of the recursion combines).  Between
+// stages the CTA re-distributes residues through shared memory, using
+// layouts chosen so that every warp access is free of bank conflicts.
+//
+//  * k_tile4096: one contiguous tile of 4096 residues (a node of level m-12)
+//    of one prime; halving levels 0-3 / 4-7 / 8-10 of the tile, the 2x2 leaf
+//    products, and the recombination back up.  Twiddles of levels 0-7 are
+//    generated once per CTA into shared memory, those of levels 8-10 by each
+//    thread for its own subtree (plan.cu explains the factorisation).
+//  * k_colfwd<LF> / k_colinv<LF, NP>: LF (8..12) top levels of the whole
+//    array, over 4 adjacent columns of 2^LF rows per CTA; the inverse pass
+//    can carry all three primes of a polynomial product and finish with the
+//    CRT.
+#include <atomic>
+
+#include "common.hpp"
+#include "kernels_mod.hpp"
+#include "prof.hpp"
+
+namespace fcirc {
+
+// Source modes are compile-time so that every load loop is branch-free and
+// all of a thread's loads can be in flight together:
+//   bits 0-1: SrcKind; bit 2: multiply by Src::scale on load;
+//   bits 3-4: zero half of a first pass (1: below N/2, 2: from N/2).
+enum : int {
+    MODE_U32 = SRC_U32,
+    MODE_U32_S = SRC_U32 | 4,
+    MODE_REV_S = SRC_U16_REV | 4,
+    MODE_REV_S_H = SRC_U16_REV | 4 | (1 << 3),
+    MODE_U16 = SRC_U16,
+    MODE_U16_H = SRC_U16 | (2 << 3),
+};
+
+template <int MODE>
+__device__ __forceinline__ uint32_t ld_raw(const Src &s, uint32_t N, uint32_t idx)
+{
+    constexpr int KIND = MODE & 3;
+    if constexpr (KIND == SRC_U32) {
+        return static_cast<const uint32_t *>(s.ptr)[idx];
+    } else if constexpr (KIND == SRC_U16_REV) {
+        const uint32_t j = N - 1 - idx;   // a'[idx] = P[N-1-idx], P zero-padded
+        return j < s.len ? (uint32_t) static_cast<const uint16_t *>(s.ptr)[j] : 0u;
+    } else {
+        return idx < s.len ? (uint32_t) static_cast<const uint16_t *>(s.ptr)[idx] : 0u;
+    }
+}
+
+template <int MODE>
+__device__ __forceinline__ uint32_t ld_scale(uint32_t v, const Src &s, uint32_t p)
+{
+    if constexpr ((MODE & 4) != 0)
+        return shoup_mul(v, s.scale.w, s.scale.wp, p);
+    else
+        return v;
+}
+
+// ---------------------------------------------------------------------------
+// register stages.  A group of 2^NL registers v[0..2^NL) is the subtree of one
+// node: local level d pairs v[k] with v[k + h], h = 2^(NL-d-1), inside local
+// node j = k >> (NL - d); tw(d, j) is that node's twiddle (or its inverse).
+
+template <int NL, int NLEV, class TwFn>
+__device__ __forceinline__ void fwd2(uint32_t *a, uint32_t *x, TwFn tw, uint32_t p, uint32_t p2)
+{
+#pragma unroll
+    for (int d = 0; d < NLEV; ++d) {
+        const int h = (1 << NL) >> (d + 1);
+#pragma unroll
+        for (int j = 0; j < (1 << d); ++j) {
+            const Tw s = tw(d, j);
+#pragma unroll
+            for (int i = 0; i < h; ++i) {
+                const int lo = (j << (NL - d)) + i;
+                bfly_row(a[lo], a[lo + h], s, p, p2);
+                bfly_vec(x[lo], x[lo + h], s, p, p2);
+            }
+        }
+    }
+}
+
+template <int NL, bool VEC, class TwFn>
+__device__ __forceinline__ void fwd1(uint32_t *v, TwFn tw, uint32_t p, uint32_t p2)
+{
+#pragma unroll
+    for (int d = 0; d < NL; ++d) {
+        const int h = (1 << NL) >> (d + 1);
+#pragma unroll
+        for (int j = 0; j < (1 << d); ++j) {
+            const Tw s = tw(d, j);
+#pragma unroll
+            for (int i = 0; i < h; ++i) {
+                const int lo = (j << (NL - d)) + i;
+                if (VEC)
+                    bfly_vec(v[lo], v[lo + h], s, p, p2);
+                else
+                    bfly_row(v[lo], v[lo + h], s, p, p2);
+            }
+        }
+    }
+}
+
+// recombination, local levels NLEV-1 .. 0
+template <int NL, int NLEV, class TwFn>
+__device__ __forceinline__ void rec1(uint32_t *v, TwFn tw, uint32_t p, uint32_t p2)
+{
+#pragma unroll
+    for (int d = NLEV - 1; d >= 0; --d) {
+        const int h = (1 << NL) >> (d + 1);
+#pragma unroll
+        for (int j = 0; j < (1 << d); ++j) {
+            const Tw s = tw(d, j);
+#pragma unroll
+            for (int i = 0; i < h; ++i) {
+                const int lo = (j << (NL - d)) + i;
+                bfly_rec(v[lo], v[lo + h], s, p, p2);
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// tile kernel, 4096 residues, 256 threads
+
+// Shared-memory position of tile element e: 128-bit chunks (e >> 2) are
+// permuted inside each 128-byte row by an XOR with bits of the row index, so
+// that the three access patterns (stride 256, the 16 x 16 transpose and the
+// contiguous 16-residue groups read as 128-bit vectors) are conflict-free.
+__device__ __forceinline__ int tphi(int e)
+{
+    const int c = e >> 2, r = c >> 3, col = c & 7;
+    const int g = (r & 3) ^ ((r & 8) >> 1);
+    return (((r << 3) | (col ^ g)) << 2) | (e & 3);
+}
+
+template <int MA, int MX>
+__global__ void __launch_bounds__(256, 3) k_tile4096(const __grid_constant__ TileParams P)
+{
+    __shared__ __align__(16) uint32_t SA[4096];
+    __shared__ __align__(16) uint32_t SX[4096];
+    __shared__ Tw STW[256];
+    __shared__ Tw SITW[256];
+    const TileJob &J = P.job[blockIdx.y];
+    const uint32_t p = J.p, p2 = 2 * J.p, pinv = J.pinv;
+    const int tid = threadIdx.x;
+    const uint64_t t = blockIdx.x;
+    const uint64_t base = t << 12;
+    const uint32_t *sg = J.sig + t * (uint64_t)(11 * 6);   // D = 11 levels
+
+    // twiddles of tile levels 0..7 (heap index 1..255), one per thread
+    if (tid > 0) {
+        const int d = 31 - __clz(tid);
+        const uint32_t *e = sg + d * 6;
+        STW[tid] = twiddle_from(J.U[tid], e[0], e[1], e[2], p);
+        SITW[tid] = twiddle_from(J.Ui[tid], e[3], e[4], e[5], p);
+    }
+    uint32_t a[16], x[16];
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+        a[j] = ld_raw<MA>(J.a, (uint32_t)P.N, (uint32_t)base + tid + 256 * j);
+        x[j] = ld_raw<MX>(J.x, (uint32_t)P.N, (uint32_t)base + tid + 256 * j);
+    }
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+        a[j] = ld_scale<MA>(a[j], J.a, p);
+        x[j] = ld_scale<MX>(x[j], J.x, p);
+    }
+    __syncthreads();
+
+    // stage A: tile levels 0..3, residues tid + 256 j
+    fwd2<4, 4>(a, x, [&](int d, int j) { return STW[(1 << d) + j]; }, p, p2);
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+        SA[tphi(tid + 256 * j)] = a[j];
+        SX[tphi(tid + 256 * j)] = x[j];
+    }
+    __syncthreads();
+    // stage B: levels 4..7, residues 256 (tid >> 4) + 16 m + (tid & 15)
+    const int eb = ((tid >> 4) << 8) + (tid & 15);
+#pragma unroll
+    for (int m = 0; m < 16; ++m) {
+        a[m] = SA[tphi(eb + 16 * m)];
+        x[m] = SX[tphi(eb + 16 * m)];
+    }
+    const int nb = tid >> 4;
+    fwd2<4, 4>(a, x, [&](int d, int j) { return STW[(1 << (4 + d)) + (nb << d) + j]; }, p, p2);
+    __syncthreads();
+#pragma unroll
+    for (int m = 0; m < 16; ++m) {
+        SA[tphi(eb + 16 * m)] = a[m];
+        SX[tphi(eb + 16 * m)] = x[m];
+    }
+    __syncthreads();
+    // stage C: levels 8..10 and the leaves, residues 16 tid .. 16 tid + 15
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const uint4 va = *reinterpret_cast<const uint4 *>(&SA[tphi(16 * tid + 4 * q)]);
+        const uint4 vx = *reinterpret_cast<const uint4 *>(&SX[tphi(16 * tid + 4 * q)]);
+        a[4 * q] = va.x; a[4 * q + 1] = va.y; a[4 * q + 2] = va.z; a[4 * q + 3] = va.w;
+        x[4 * q] = vx.x; x[4 * q + 1] = vx.y; x[4 * q + 2] = vx.z; x[4 * q + 3] = vx.w;
+    }
+    Tw tc[7];   // this thread's nodes: level 8 (tid), 9 (2 tid + r), 10 (4 tid + r)
+    {
+        const uint32_t *e8 = sg + 8 * 6, *e9 = sg + 9 * 6, *e10 = sg + 10 * 6;
+        tc[0] = twiddle_from(J.U[256 + tid], e8[0], e8[1], e8[2], p);
+#pragma unroll
+        for (int r = 0; r < 2; ++r) tc[1 + r] = twiddle_from(J.U[512 + 2 * tid + r], e9[0], e9[1], e9[2], p);
+#pragma unroll
+        for (int r = 0; r < 4; ++r) tc[3 + r] = twiddle_from(J.U[1024 + 4 * tid + r], e10[0], e10[1], e10[2], p);
+    }
+    fwd2<4, 3>(a, x, [&](int d, int j) { return tc[(1 << d) - 1 + j]; }, p, p2);
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+        Tw phi = tc[3 + (q >> 1)];
+        if (q & 1) phi = tw_neg(phi, p);
+        leaf2(a[2 * q], a[2 * q + 1], x[2 * q], x[2 * q + 1], phi, p, p2, pinv);
+    }
+    {
+        const uint32_t *e8 = sg + 8 * 6, *e9 = sg + 9 * 6, *e10 = sg + 10 * 6;
+        tc[0] = twiddle_from(J.Ui[256 + tid], e8[3], e8[4], e8[5], p);
+#pragma unroll
+        for (int r = 0; r < 2; ++r) tc[1 + r] = twiddle_from(J.Ui[512 + 2 * tid + r], e9[3], e9[4], e9[5], p);
+#pragma unroll
+        for (int r = 0; r < 4; ++r) tc[3 + r] = twiddle_from(J.Ui[1024 + 4 * tid + r], e10[3], e10[4], e10[5], p);
+    }
+    rec1<4, 3>(a, [&](int d, int j) { return tc[(1 << d) - 1 + j]; }, p, p2);
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+        *reinterpret_cast<uint4 *>(&SA[tphi(16 * tid + 4 * q)]) =
+            make_uint4(a[4 * q], a[4 * q + 1], a[4 * q + 2], a[4 * q + 3]);
+    __syncthreads();
+#pragma unroll
+    for (int m = 0; m < 16; ++m) a[m] = SA[tphi(eb + 16 * m)];
+    rec1<4, 4>(a, [&](int d, int j) { return SITW[(1 << (4 + d)) + (nb << d) + j]; }, p, p2);
+    __syncthreads();
+#pragma unroll
+    for (int m = 0; m < 16; ++m) SA[tphi(eb + 16 * m)] = a[m];
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < 16; ++j) a[j] = SA[tphi(tid + 256 * j)];
+    rec1<4, 4>(a, [&](int d, int j) { return SITW[(1 << d) + j]; }, p, p2);
+#pragma unroll
+    for (int j = 0; j < 16; ++j) J.dst[base + tid + 256 * j] = J.store_lazy ? a[j] : reduce_once(a[j], p);
+}
+
+// ---------------------------------------------------------------------------
+// column passes: 2^LF rows x 4 adjacent columns per CTA, 2^LF / 8 threads,
+// each thread owning 32 residues of a stage (two batches of 16 registers)
+
+// Shared-memory word of (row r, column c): rows are permuted inside aligned
+// groups of 8 by an XOR with bits 4..6 of the row, so that both consecutive
+// rows and rows 16 apart fall into distinct banks.
+__device__ __forceinline__ int cphi(int r, int c) { return ((r ^ ((r >> 4) & 7)) << 2) | c; }
+
+template <int LF>
+struct ColShape {
+    static constexpr int R = 1 << LF;
+    static constexpr int NT = R / 8;
+    static constexpr int NST = (LF + 3) / 4;
+    static constexpr int NL0 = LF - 4 * (NST - 1);   // the first stage takes the remainder
+    static constexpr int nl(int s) { return s == 0 ? NL0 : 4; }
+    static constexpr int d0(int s) { return s == 0 ? 0 : NL0 + 4 * (s - 1); }
+};
+
+// Twiddles of local level D of one group (group-ordered table, see
+// kernels_mod.hpp), read with 128-bit loads.
+template <int D>
+__device__ __forceinline__ void load_level(const Tw *g, Tw *tl)
+{
+    if constexpr (D == 0) {
+        const uint2 v = __ldg(reinterpret_cast<const uint2 *>(g + 14));
+        tl[0] = Tw{v.x, v.y};
+    } else {
+        const uint4 *q = reinterpret_cast<const uint4 *>(g + 16 - (2 << D));
+#pragma unroll
+        for (int k = 0; k < (1 << (D - 1)); ++k) {
+            const uint4 v = __ldg(q + k);
+            tl[2 * k] = Tw{v.x, v.y};
+            tl[2 * k + 1] = Tw{v.z, v.w};
+        }
+    }
+}
+
+// levels D .. NL-1 of one group of 2^NL registers (both input sides)
+template <int NL, int D, bool VEC>
+__device__ __forceinline__ void fwd_levels(uint32_t *v, const Tw *g, uint32_t p, uint32_t p2)
+{
+    if constexpr (D < NL) {
+        Tw tl[1 << D];
+        load_level<D>(g, tl);
+        constexpr int h = (1 << NL) >> (D + 1);
+#pragma unroll
+        for (int j = 0; j < (1 << D); ++j)
+#pragma unroll
+            for (int i = 0; i < h; ++i) {
+                const int lo = (j << (NL - D)) + i;
+                if (VEC)
+                    bfly_vec(v[lo], v[lo + h], tl[j], p, p2);
+                else
+                    bfly_row(v[lo], v[lo + h], tl[j], p, p2);
+            }
+        fwd_levels<NL, D + 1, VEC>(v, g, p, p2);
+    }
+}
+
+// recombination levels D .. 0 of one group (inverse twiddles)
+template <int NL, int D>
+__device__ __forceinline__ void rec_levels(uint32_t *v, const Tw *g, uint32_t p, uint32_t p2)
+{
+    if constexpr (D >= 0) {
+        Tw tl[1 << D];
+        load_level<D>(g, tl);
+        constexpr int h = (1 << NL) >> (D + 1);
+#pragma unroll
+        for (int j = 0; j < (1 << D); ++j)
+#pragma unroll
+            for (int i = 0; i < h; ++i) {
+                const int lo = (j << (NL - D)) + i;
+                bfly_rec(v[lo], v[lo + h], tl[j], p, p2);
+            }
+        rec_levels<NL, D - 1>(v, g, p, p2);
+    }
+}
+
+// Group slot h of thread tid in stage (D0, NL): column, first row, and the
+// level-D0 block the group lies in; members are row0 + i 2^LST.
+template <int LF, int D0, int NL>
+__device__ __forceinline__ void col_group(int tid, int h, int &col, int &row0, int &blk)
+{
+    constexpr int NT = ColShape<LF>::NT;
+    constexpr int LST = LF - D0 - NL;
+    constexpr int LRB = LF - D0;
+    const int gg = tid + NT * h;
+    col = gg & 3;
+    const int g = gg >> 2;
+    blk = g >> LST;
+    row0 = (blk << LRB) + (g & ((1 << LST) - 1));
+}
+
+template <int LF, int S, int MODE>
+__device__ __forceinline__ void colfwd_stage(const ColFwdJob &J, const ColFwdParams &P, uint32_t *sm,
+                                             uint32_t base, uint32_t pb, int logS, int tid)
+{
+    constexpr int half = (S == 0) ? ((MODE >> 3) & 3) : 0;
+    using Sh = ColShape<LF>;
+    constexpr int NL = Sh::nl(S), D0 = Sh::d0(S);
+    constexpr int M = 1 << NL, B = 16 >> NL, LST = LF - D0 - NL;
+    constexpr bool FIRST = (S == 0), LAST = (S == Sh::NST - 1);
+    const uint32_t p = J.p, p2 = 2 * J.p;
+    const Tw *gt = J.gtw + P.stage_off[S];
+#pragma unroll 1
+    for (int bt = 0; bt < 2; ++bt) {
+        uint32_t v[16];
+#pragma unroll
+        for (int hb = 0; hb < B; ++hb) {
+            int col, row0, blk;
+            col_group<LF, D0, NL>(tid, bt * B + hb, col, row0, blk);
+            uint32_t *vg = v + hb * M;
+            if constexpr (FIRST && half == 1) {
+                // input zero in rows < R/2, level 0 has s = 1: (0 + hi, 0 - hi)
+#pragma unroll
+                for (int i = M / 2; i < M; ++i)
+                    vg[i] = ld_raw<MODE>(J.src, P.N, base + ((row0 + (i << LST)) << logS) + col);
+#pragma unroll
+                for (int i = M / 2; i < M; ++i) {
+                    const uint32_t t = ld_scale<MODE>(vg[i], J.src, p);
+                    vg[i - M / 2] = t;
+                    vg[i] = p2 - t;
+                }
+            } else if constexpr (FIRST && half == 2) {
+                // input zero in rows >= R/2, level 0 has s = 1: (lo, lo)
+#pragma unroll
+                for (int i = 0; i < M / 2; ++i)
+                    vg[i] = ld_raw<MODE>(J.src, P.N, base + ((row0 + (i << LST)) << logS) + col);
+#pragma unroll
+                for (int i = 0; i < M / 2; ++i) {
+                    vg[i] = ld_scale<MODE>(vg[i], J.src, p);
+                    vg[i + M / 2] = vg[i];
+                }
+            } else if constexpr (FIRST) {
+#pragma unroll
+                for (int i = 0; i < M; ++i)
+                    vg[i] = ld_raw<MODE>(J.src, P.N, base + ((row0 + (i << LST)) << logS) + col);
+#pragma unroll
+                for (int i = 0; i < M; ++i) vg[i] = ld_scale<MODE>(vg[i], J.src, p);
+            } else {
+#pragma unroll
+                for (int i = 0; i < M; ++i) vg[i] = sm[cphi(row0 + (i << LST), col)];
+            }
+        }
+#pragma unroll
+        for (int hb = 0; hb < B; ++hb) {
+            int col, row0, blk;
+            col_group<LF, D0, NL>(tid, bt * B + hb, col, row0, blk);
+            const Tw *g = gt + (((pb << D0) + blk) << 4);
+            uint32_t *vg = v + hb * M;
+            if constexpr (FIRST && half != 0) {
+                if (J.vec_side)
+                    fwd_levels<NL, 1, true>(vg, g, p, p2);
+                else
+                    fwd_levels<NL, 1, false>(vg, g, p, p2);
+            } else {
+                if (J.vec_side)
+                    fwd_levels<NL, 0, true>(vg, g, p, p2);
+                else
+                    fwd_levels<NL, 0, false>(vg, g, p, p2);
+            }
+        }
+#pragma unroll
+        for (int hb = 0; hb < B; ++hb) {
+            int col, row0, blk;
+            col_group<LF, D0, NL>(tid, bt * B + hb, col, row0, blk);
+#pragma unroll
+            for (int i = 0; i < M; ++i) {
+                const uint32_t row = row0 + (i << LST);
+                if (LAST)
+                    J.dst[base + (row << logS) + col] = v[hb * M + i];
+                else
+                    sm[cphi(row, col)] = v[hb * M + i];
+            }
+        }
+    }
+}
+
+template <int LF, int MODE>
+__device__ __forceinline__ void colfwd_jobs(const ColFwdParams &P, uint32_t *sm, int j0, uint32_t base,
+                                            uint32_t pb, int logS, int tid)
+{
+    using Sh = ColShape<LF>;
+#pragma unroll 1
+    for (int jj = 0; jj < P.jobs_per_cta; ++jj) {
+        const ColFwdJob &J = P.job[j0 + jj];
+        if (jj > 0) __syncthreads();   // the previous job's last reads of sm are done
+        colfwd_stage<LF, 0, MODE>(J, P, sm, base, pb, logS, tid);
+        if constexpr (Sh::NST > 1) {
+            __syncthreads();
+            colfwd_stage<LF, 1, MODE>(J, P, sm, base, pb, logS, tid);
+        }
+        if constexpr (Sh::NST > 2) {
+            __syncthreads();
+            colfwd_stage<LF, 2, MODE>(J, P, sm, base, pb, logS, tid);
+        }
+    }
+}
+
+// blockIdx.y selects a group of jobs_per_cta jobs; group 0 reads its input
+// in mode M0, group 1 in mode M1
+template <int LF, int M0, int M1>
+__global__ void __launch_bounds__(ColShape<LF>::NT, 2) k_colfwd(const __grid_constant__ ColFwdParams P)
+{
+    extern __shared__ __align__(16) uint32_t sm[];
+    using Sh = ColShape<LF>;
+    const int tid = threadIdx.x;
+    const int logS = P.logn - P.l1;
+    const int cg_bits = logS - 2;
+    const uint32_t pb = blockIdx.x >> cg_bits;
+    const uint32_t cg = blockIdx.x & ((1u << cg_bits) - 1);
+    const uint32_t base = (pb << (P.logn - P.l0)) + (cg << 2);
+    const int j0 = blockIdx.y * P.jobs_per_cta;
+    if (blockIdx.y == 0)
+        colfwd_jobs<LF, M0>(P, sm, j0, base, pb, logS, tid);
+    else
+        colfwd_jobs<LF, M1>(P, sm, j0, base, pb, logS, tid);
+}
+
+template <int LF, int NP, int S>
+__device__ __forceinline__ void colinv_stage(const ColInvParams &P, uint32_t *sm, uint32_t base,
+                                             uint32_t pb, int logS, int tid)
+{
+    using Sh = ColShape<LF>;
+    constexpr int NL = Sh::nl(S), D0 = Sh::d0(S);
+    constexpr int M = 1 << NL, B = 16 >> NL, LST = LF - D0 - NL;
+    constexpr bool FIRST = (S == Sh::NST - 1), LAST = (S == 0);
+    constexpr int R = 1 << LF;
+#pragma unroll 1
+    for (int q = 0; q < NP; ++q) {
+        const ColInvJob &J = P.job[q];
+        const uint32_t p = J.p, p2 = 2 * J.p;
+        uint32_t *smq = sm + q * (R * 4);
+        const Tw *gt = J.gitw + P.stage_off[S];
+#pragma unroll 1
+        for (int bt = 0; bt < 2; ++bt) {
+            uint32_t v[16];
+#pragma unroll
+            for (int hb = 0; hb < B; ++hb) {
+                int col, row0, blk;
+                col_group<LF, D0, NL>(tid, bt * B + hb, col, row0, blk);
+#pragma unroll
+                for (int i = 0; i < M; ++i) {
+                    const uint32_t row = row0 + (i << LST);
+                    v[hb * M + i] = FIRST ? J.src[base + (row << logS) + col] : smq[cphi(row, col)];
+                }
+            }
+#pragma unroll
+            for (int hb = 0; hb < B; ++hb) {
+                int col, row0, blk;
+                col_group<LF, D0, NL>(tid, bt * B + hb, col, row0, blk);
+                rec_levels<NL, NL - 1>(v + hb * M, gt + (((pb << D0) + blk) << 4), p, p2);
+            }
+#pragma unroll
+            for (int hb = 0; hb < B; ++hb) {
+                int col, row0, blk;
+                col_group<LF, D0, NL>(tid, bt * B + hb, col, row0, blk);
+#pragma unroll
+                for (int i = 0; i < M; ++i) {
+                    const uint32_t row = row0 + (i << LST);
+                    const uint32_t val = v[hb * M + i];
+                    if (!LAST)
+                        smq[cphi(row, col)] = val;
+                    else if (P.epi == EPI_CRT_ROT)
+                        smq[cphi(row, col)] = reduce_once(val, p);   // canonical, for the CRT below
+                    else
+                        J.dst[base + (row << logS) + col] = P.epi == EPI_CANON ? reduce_once(val, p) : val;
+                }
+            }
+        }
+    }
+    if (LAST && NP == 3 && P.epi == EPI_CRT_ROT) {
+        // every residue of this thread's groups was written by this thread
+        const uint32_t mask = P.N - 1;
+#pragma unroll 1
+        for (int h = 0; h < 2 * B; ++h) {
+            int col, row0, blk;
+            col_group<LF, D0, NL>(tid, h, col, row0, blk);
+#pragma unroll 4
+            for (int i = 0; i < M; ++i) {
+                const uint32_t row = row0 + (i << LST);
+                const int w = cphi(row, col);
+                const uint32_t idx = base + (row << logS) + col;
+                const uint32_t dst = (idx + mask) & mask;   // c_k = d_{k+1}
+                if (dst < P.nout) P.dst64[dst] = crt3(sm[w], sm[R * 4 + w], sm[2 * R * 4 + w], P.crt);
+            }
+        }
+    }
+}
+
+template <int LF, int NP>
+__global__ void __launch_bounds__(ColShape<LF>::NT) k_colinv(const __grid_constant__ ColInvParams P)
+{
+    extern __shared__ __align__(16) uint32_t sm[];
+    using Sh = ColShape<LF>;
+    const int tid = threadIdx.x;
+    const int logS = P.logn - P.l1;
+    const int cg_bits = logS - 2;
+    const uint32_t pb = blockIdx.x >> cg_bits;
+    const uint32_t cg = blockIdx.x & ((1u << cg_bits) - 1);
+    const uint32_t base = (pb << (P.logn - P.l0)) + (cg << 2);
+    if constexpr (Sh::NST > 2) {
+        colinv_stage<LF, NP, 2>(P, sm, base, pb, logS, tid);
+        __syncthreads();
+    }
+    if constexpr (Sh::NST > 1) {
+        colinv_stage<LF, NP, 1>(P, sm, base, pb, logS, tid);
+        __syncthreads();
+    }
+    colinv_stage<LF, NP, 0>(P, sm, base, pb, logS, tid);
+}
+
+// ---------------------------------------------------------------------------
+// launchers
+
+template <class K>
+static int ensure_smem_f(K kernel, int bytes, std::atomic<unsigned> &mask)
+{
+    int dev = 0;
+    FCIRC_CUDA_TRY(cudaGetDevice(&dev));
+    const unsigned bit = 1u << (dev & 31);
+    if (mask.load() & bit) return FCIRC_OK;
+    FCIRC_CUDA_TRY(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+    mask.fetch_or(bit);
+    return FCIRC_OK;
+}
+
+bool fast_tile_ok(int logT) { return logT == 12; }
+bool fast_col_ok(int lf, int logS) { return lf >= 8 && lf <= 12 && logS >= 2; }
+
+static int src_mode(const Src &s, int half)
+{
+    return s.kind | (s.scaled ? 4 : 0) | (half << 3);
+}
+
+int launch_tile_fast(const TileParams &P, uint64_t ntiles, int njobs, cudaStream_t s)
+{
+    dim3 grid((unsigned)ntiles, njobs);
+    const int ma = src_mode(P.job[0].a, 0), mx = src_mode(P.job[0].x, 0);
+    ProfScope ps("k_tile4096", s);
+    if (ma == MODE_U32 && mx == MODE_U32)
+        k_tile4096<MODE_U32, MODE_U32><<<grid, 256, 0, s>>>(P);
+    else if (ma == MODE_U32_S && mx == MODE_U32)
+        k_tile4096<MODE_U32_S, MODE_U32><<<grid, 256, 0, s>>>(P);
+    else if (ma == MODE_REV_S && mx == MODE_U16)
+        k_tile4096<MODE_REV_S, MODE_U16><<<grid, 256, 0, s>>>(P);
+    else
+        return fail(FCIRC_EINVAL, "tile kernel: unsupported source modes %d/%d", ma, mx);
+    FCIRC_CUDA_TRY(cudaGetLastError());
+    return FCIRC_OK;
+}
+
+template <int LF, int M0, int M1>
+static int launch_colfwd_m(const ColFwdParams &P, int nctay, cudaStream_t s)
+{
+    static std::atomic<unsigned> mask{0};
+    const int smem = (1 << LF) * 4 * 4;
+    FCIRC_TRY(ensure_smem_f(k_colfwd<LF, M0, M1>, smem, mask));
+    const uint64_t ncta = (uint64_t)1 << (P.l0 + (P.logn - P.l1) - 2);
+    dim3 grid((unsigned)ncta, nctay);
+    ProfScope ps("k_colfwd", s);
+    k_colfwd<LF, M0, M1><<<grid, ColShape<LF>::NT, smem, s>>>(P);
+    FCIRC_CUDA_TRY(cudaGetLastError());
+    return FCIRC_OK;
+}
+
+template <int LF>
+static int launch_colfwd_lf(const ColFwdParams &P, int nctay, cudaStream_t s)
+{
+    const int m0 = src_mode(P.job[0].src, P.job[0].half);
+    const int m1 = nctay > 1 ? src_mode(P.job[P.jobs_per_cta].src, P.job[P.jobs_per_cta].half) : MODE_U32;
+    for (int g = 0; g < nctay; ++g)
+        for (int k = 0; k < P.jobs_per_cta; ++k) {
+            const ColFwdJob &J = P.job[g * P.jobs_per_cta + k];
+            if (src_mode(J.src, J.half) != (g == 0 ? m0 : m1))
+                return fail(FCIRC_EINVAL, "column pass: mixed source modes in one job group");
+        }
+    if (m0 == MODE_U32_S && m1 == MODE_U32) return launch_colfwd_m<LF, MODE_U32_S, MODE_U32>(P, nctay, s);
+    if (m0 == MODE_U32 && m1 == MODE_U32) return launch_colfwd_m<LF, MODE_U32, MODE_U32>(P, nctay, s);
+    if (m0 == MODE_REV_S_H && m1 == MODE_U16_H) return launch_colfwd_m<LF, MODE_REV_S_H, MODE_U16_H>(P, nctay, s);
+    if (m0 == MODE_REV_S && m1 == MODE_U16) return launch_colfwd_m<LF, MODE_REV_S, MODE_U16>(P, nctay, s);
+    return fail(FCIRC_EINVAL, "column pass: unsupported source modes %d/%d", m0, m1);
+}
+
+int launch_colfwd(const ColFwdParams &P, int nctay, cudaStream_t s)
+{
+    switch (P.l1 - P.l0) {
+    case 8: return launch_colfwd_lf<8>(P, nctay, s);
+    case 9: return launch_colfwd_lf<9>(P, nctay, s);
+    case 10: return launch_colfwd_lf<10>(P, nctay, s);
+    case 11: return launch_colfwd_lf<11>(P, nctay, s);
+    case 12: return launch_colfwd_lf<12>(P, nctay, s);
+    default: return fail(FCIRC_EINVAL, "column pass of %d levels", P.l1 - P.l0);
+    }
+}
+
+template <int LF, int NP>
+static int launch_colinv_lf(const ColInvParams &P, cudaStream_t s)
+{
+    static std::atomic<unsigned> mask{0};
+    const int smem = NP * (1 << LF) * 4 * 4;
+    FCIRC_TRY(ensure_smem_f(k_colinv<LF, NP>, smem, mask));
+    const uint64_t ncta = (uint64_t)1 << (P.l0 + (P.logn - P.l1) - 2);
+    ProfScope ps("k_colinv", s);
+    k_colinv<LF, NP><<<(unsigned)ncta, ColShape<LF>::NT, smem, s>>>(P);
+    FCIRC_CUDA_TRY(cudaGetLastError());
+    return FCIRC_OK;
+}
+
+int launch_colinv(const ColInvParams &P, cudaStream_t s)
+{
+    const int lf = P.l1 - P.l0;
+    if (P.nprime == 1) {
+        switch (lf) {
+        case 8: return launch_colinv_lf<8, 1>(P, s);
+        case 9: return launch_colinv_lf<9, 1>(P, s);
+        case 10: return launch_colinv_lf<10, 1>(P, s);
+        case 11: return launch_colinv_lf<11, 1>(P, s);
+        case 12: return launch_colinv_lf<12, 1>(P, s);
+        }
+    } else if (P.nprime == 3) {
+        switch (lf) {
+        case 8: return launch_colinv_lf<8, 3>(P, s);
+        case 9: return launch_colinv_lf<9, 3>(P, s);
+        case 10: return launch_colinv_lf<10, 3>(P, s);
+        case 11: return launch_colinv_lf<11, 3>(P, s);
+        case 12: return launch_colinv_lf<12, 3>(P, s);
+        }
+    }
+    return fail(FCIRC_EINVAL, "column pass of %d levels, %d primes", lf, P.nprime);
+}
+
+}  // namespace fcirc

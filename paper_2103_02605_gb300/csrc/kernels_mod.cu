@@ -27,19 +27,23 @@
 
 namespace fcirc {
 
-__device__ __forceinline__ uint32_t load_src(const Src &s, uint64_t N, uint64_t idx)
+__device__ __forceinline__ uint32_t load_src(const Src &s, uint64_t N, uint64_t idx, uint32_t p)
 {
+    uint32_t v;
     switch (s.kind) {
     case SRC_U32:
-        return static_cast<const uint32_t *>(s.ptr)[idx];
+        v = static_cast<const uint32_t *>(s.ptr)[idx];
+        break;
     case SRC_U16_REV: {
         // a'[idx] = P[N-1-idx] with P zero-padded to N
         uint64_t j = N - 1 - idx;
-        return j < s.len ? static_cast<const uint16_t *>(s.ptr)[j] : 0u;
+        v = j < s.len ? static_cast<const uint16_t *>(s.ptr)[j] : 0u;
+        break;
     }
     default:  // SRC_U16
-        return idx < s.len ? static_cast<const uint16_t *>(s.ptr)[idx] : 0u;
+        v = idx < s.len ? static_cast<const uint16_t *>(s.ptr)[idx] : 0u;
     }
+    return s.scaled ? shoup_mul(v, s.scale.w, s.scale.wp, p) : v;
 }
 
 // ---------------------------------------------------------------------------
@@ -61,8 +65,8 @@ k_tile(const __grid_constant__ TileParams P)
     const uint64_t base = t << logT;
 
     for (int i = threadIdx.x; i < T; i += blockDim.x) {
-        A[i] = load_src(J.a, P.N, base + i);
-        X[i] = load_src(J.x, P.N, base + i);
+        A[i] = load_src(J.a, P.N, base + i, p);
+        X[i] = load_src(J.x, P.N, base + i, p);
     }
     if (D > 0) {
         const uint32_t *sg = J.sig + t * (uint64_t)D * 6;
@@ -104,7 +108,7 @@ k_tile(const __grid_constant__ TileParams P)
             if (e & 1) phi = tw_neg(phi, p);
         }
         uint32_t a0 = A[2 * e], a1 = A[2 * e + 1];
-        leaf2(a0, a1, X[2 * e], X[2 * e + 1], phi, J.kt, p, p2, pinv);
+        leaf2(a0, a1, X[2 * e], X[2 * e + 1], phi, p, p2, pinv);
         A[2 * e] = a0;
         A[2 * e + 1] = a1;
     }
@@ -147,7 +151,7 @@ k_strided_fwd(const __grid_constant__ StrFwdParams P)
 
     for (int e = threadIdx.x; e < RW; e += blockDim.x) {
         const int r = e >> logW, w = e & (W - 1);
-        tile[e] = load_src(J.src, P.N, base + ((uint64_t)r << logS) + w);
+        tile[e] = load_src(J.src, P.N, base + ((uint64_t)r << logS) + w, p);
     }
     __syncthreads();
     for (int d = 0; d < logR; ++d) {
@@ -175,17 +179,6 @@ k_strided_fwd(const __grid_constant__ StrFwdParams P)
     }
 }
 
-__device__ __forceinline__ uint64_t crt3(uint32_t r1, uint32_t r2, uint32_t r3, const CrtConsts &C)
-{
-    // Garner: x = r1 + p1 t2 + p1 p2 t3 with x = r_i (mod p_i), all r_i canonical
-    const uint32_t r1m2 = reduce_once(shoup_mul(r1, 1u, C.m2, C.p2), C.p2);
-    const uint32_t t2 = reduce_once(shoup_mul(r2 + C.p2 - r1m2, C.inv12.w, C.inv12.wp, C.p2), C.p2);
-    const uint32_t r1m3 = reduce_once(shoup_mul(r1, 1u, C.m3, C.p3), C.p3);
-    uint32_t u = r1m3 + reduce_once(shoup_mul(t2, C.p1m3.w, C.p1m3.wp, C.p3), C.p3);
-    u = reduce_once(u, C.p3);
-    const uint32_t t3 = reduce_once(shoup_mul(r3 + C.p3 - u, C.inv123.w, C.inv123.wp, C.p3), C.p3);
-    return (uint64_t)r1 + (uint64_t)C.p1 * t2 + C.p1p2 * (uint64_t)t3;
-}
 
 __global__ void __launch_bounds__(kStrThreads)
 k_strided_inv(const __grid_constant__ StrInvParams P)

@@ -15,11 +15,14 @@ enum SrcKind { SRC_U32 = 0, SRC_U16_REV = 1, SRC_U16 = 2 };
 
 // Where a pass reads its input: a uint32 array (residues), or 16-bit
 // coefficients zero-padded to the transform length, optionally reversed
-// (a'[i] = P[N-1-i]) for the row vector of a polynomial product.
+// (a'[i] = P[N-1-i]) for the row vector of a polynomial product.  The first
+// load of the row vector multiplies it by `scale` (2^32 2^-L, see leaf2).
 struct Src {
     const void *ptr;
     uint64_t len;
     int kind;
+    int scaled;
+    Tw scale;
 };
 
 struct TileJob {
@@ -29,7 +32,6 @@ struct TileJob {
     const Tw *rho;         // plan tile roots
     const uint32_t *U, *Ui;
     uint32_t p, pinv;
-    Tw kt;
     int store_lazy;
 };
 
@@ -83,11 +85,80 @@ struct StrInvParams {
     CrtConsts crt;
 };
 
+#if defined(__CUDACC__)
+// Garner recombination of canonical residues r_i mod p_i into the integer
+// x < p1 p2 p3 with x = r_i (mod p_i); returned modulo 2^64 (exact whenever
+// x < 2^64, which holds for every coefficient the library produces).
+__device__ __forceinline__ uint64_t crt3(uint32_t r1, uint32_t r2, uint32_t r3, const CrtConsts &C)
+{
+    // Garner: x = r1 + p1 t2 + p1 p2 t3 with x = r_i (mod p_i), all r_i canonical
+    const uint32_t r1m2 = reduce_once(shoup_mul(r1, 1u, C.m2, C.p2), C.p2);
+    const uint32_t t2 = reduce_once(shoup_mul(r2 + C.p2 - r1m2, C.inv12.w, C.inv12.wp, C.p2), C.p2);
+    const uint32_t r1m3 = reduce_once(shoup_mul(r1, 1u, C.m3, C.p3), C.p3);
+    uint32_t u = r1m3 + reduce_once(shoup_mul(t2, C.p1m3.w, C.p1m3.wp, C.p3), C.p3);
+    u = reduce_once(u, C.p3);
+    const uint32_t t3 = reduce_once(shoup_mul(r3 + C.p3 - u, C.inv123.w, C.inv123.wp, C.p3), C.p3);
+    return (uint64_t)r1 + (uint64_t)C.p1 * t2 + C.p1p2 * (uint64_t)t3;
+}
+#endif
+
+// Register-staged column passes (kernels_fast.cu).  gtw: this pass's
+// twiddles in group order -- for stage s, group block gb (the level-d0 node
+// the group lies in), 16 entries at gtw[stage_off[s] + 16 gb]: local level
+// d node j at slot 16 - 2^(d+1) + j (levels 3, 2, 1, 0 at slots 0-7, 8-11,
+// 12-13, 14), so that each level is read with 128-bit loads.
+struct ColFwdJob {
+    Src src;
+    uint32_t *dst;
+    const Tw *gtw;
+    uint32_t p;
+    int vec_side;
+    int half;              // 0; 1: input zero below N/2; 2: input zero from N/2 (and s = 1 at level 0)
+};
+
+struct ColFwdParams {
+    ColFwdJob job[6];
+    int jobs_per_cta;      // 1, or 3 for the three primes of one side of a product
+    uint32_t N;
+    int logn, l0, l1;
+    int stage_off[3];
+};
+
+struct ColInvJob {
+    const uint32_t *src;
+    uint32_t *dst;
+    const Tw *gitw;
+    uint32_t p;
+};
+
+struct ColInvParams {
+    ColInvJob job[3];
+    int nprime;
+    uint32_t N;
+    int logn, l0, l1;
+    int stage_off[3];
+    int epi;
+    uint64_t *dst64;
+    uint64_t nout;
+    CrtConsts crt;
+};
+
 int launch_tile(const TileParams &P, uint64_t ntiles, int njobs, cudaStream_t s);
 int launch_strided_fwd(const StrFwdParams &P, int njobs, cudaStream_t s);
 int launch_strided_inv(const StrInvParams &P, cudaStream_t s);
 int launch_crt_rot(const uint32_t *r1, const uint32_t *r2, const uint32_t *r3, uint64_t N,
                    uint64_t *out, uint64_t nout, const CrtConsts &C, cudaStream_t s);
+// register-staged kernels (kernels_fast.cu) for the shapes they cover
+bool fast_tile_ok(int logT);
+bool fast_col_ok(int lf, int logS);
+int launch_tile_fast(const TileParams &P, uint64_t ntiles, int njobs, cudaStream_t s);
+int launch_colfwd(const ColFwdParams &P, int nctay, cudaStream_t s);
+int launch_colinv(const ColInvParams &P, cudaStream_t s);
+// stage split of a column pass of lf levels: the first stage takes lf mod 4
+// (or 4), the others 4 levels each
+inline int col_nstage(int lf) { return (lf + 3) / 4; }
+inline int col_nl(int lf, int s) { return s == 0 ? lf - 4 * (col_nstage(lf) - 1) : 4; }
+inline int col_d0(int lf, int s) { return s == 0 ? 0 : col_nl(lf, 0) + 4 * (s - 1); }
 int launch_scalar(const uint32_t *a, const uint32_t *x, uint32_t *c, uint32_t p, cudaStream_t s);
 
 }  // namespace fcirc

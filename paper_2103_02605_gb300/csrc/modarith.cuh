@@ -46,10 +46,30 @@ FCIRC_HD uint32_t shoup_mul(uint32_t x, uint32_t w, uint32_t wp, uint32_t p)
     return x * w - q * p;
 }
 
-// x in [0, 2m) -> [0, m)
+// x in [0, 2m) -> [0, m): min(x, x - m) in unsigned arithmetic (x - m wraps
+// to a large value when x < m)
 FCIRC_HD uint32_t reduce_once(uint32_t x, uint32_t m)
 {
+#if defined(__CUDA_ARCH__) && defined(FCIRC_REDUCE_MIN)
+    return umin(x, x - m);
+#else
     return x >= m ? x - m : x;
+#endif
+}
+
+// [0, 4p) -> [0, p)
+FCIRC_HD uint32_t canon4(uint32_t x, uint32_t p, uint32_t p2)
+{
+    return reduce_once(reduce_once(x, p2), p);
+}
+
+// Montgomery reduction of a 64-bit T < p 2^32: T 2^-32 mod p in (0, 2p).
+// pinv = p^-1 mod 2^32; m p agrees with T in the low word, so the low words
+// cancel exactly and only the high words are subtracted.
+FCIRC_HD uint32_t redc(uint64_t T, uint32_t p, uint32_t pinv)
+{
+    const uint32_t m = (uint32_t)T * pinv;
+    return (uint32_t)(T >> 32) - umulhi32(m, p) + p;
 }
 
 // Montgomery product x*y*2^-32 mod p in (0, 2p), valid when x*y < p*2^32
@@ -128,20 +148,23 @@ FCIRC_HD void bfly_rec(uint32_t &m1, uint32_t &m2, Tw si, uint32_t p, uint32_t p
     m2 = reduce_once(d, p2);                       // [0, 2p)
 }
 
-// 2x2 leaf: the phi-circulant [[a0, a1], [phi a1, a0]] times (y0, y1),
-// scaled by K = 2^-L (the deferred halvings) -- Definition 2 at n = 2, which
-// is what Algorithm 1 gives for 1x1 blocks.  a*, y* in [0, 4p); kt is
-// 2^32 * 2^-L mod p (undoes the Montgomery factor); outputs in [0, 2p).
-FCIRC_HD void leaf2(uint32_t &a0, uint32_t &a1, uint32_t y0, uint32_t y1, Tw phi,
-                    Tw kt, uint32_t p, uint32_t p2, uint32_t pinv)
+// 2x2 leaf: the phi-circulant [[a0, a1], [phi a1, a0]] times (y0, y1) --
+// Definition 2 at n = 2, which is what Algorithm 1 gives for 1x1 blocks.
+// Each output is one 64-bit sum of two products of canonical residues
+// (below 2 p^2 < p 2^32) reduced once by Montgomery; the factor 2^32 2^-L this
+// leaves over (2^-L being the deferred halvings of the recombination) is put
+// on the row-vector input when it is first loaded.  a*, y* in [0, 4p);
+// outputs in (0, 2p).
+FCIRC_HD void leaf2(uint32_t &a0, uint32_t &a1, uint32_t y0, uint32_t y1, Tw phi, uint32_t p,
+                    uint32_t p2, uint32_t pinv)
 {
-    uint32_t x0 = reduce_once(a0, p2), x1 = reduce_once(a1, p2);
-    uint32_t z0 = reduce_once(y0, p2), z1 = reduce_once(y1, p2);
-    uint32_t x1f = shoup_mul(x1, phi.w, phi.wp, p);             // [0, 2p)
-    uint32_t c0 = mont_mul(x0, z0, p, pinv) + mont_mul(x1, z1, p, pinv);   // (0, 4p)
-    uint32_t c1 = mont_mul(x1f, z0, p, pinv) + mont_mul(x0, z1, p, pinv);
-    a0 = shoup_mul(c0, kt.w, kt.wp, p);
-    a1 = shoup_mul(c1, kt.w, kt.wp, p);
+    const uint32_t x0 = canon4(a0, p, p2), x1 = canon4(a1, p, p2);
+    const uint32_t z0 = canon4(y0, p, p2), z1 = canon4(y1, p, p2);
+    const uint32_t x1f = reduce_once(shoup_mul(x1, phi.w, phi.wp, p), p);
+    const uint64_t t0 = (uint64_t)x0 * z0 + (uint64_t)x1 * z1;
+    const uint64_t t1 = (uint64_t)x1f * z0 + (uint64_t)x0 * z1;
+    a0 = redc(t0, p, pinv);
+    a1 = redc(t1, p, pinv);
 }
 
 }  // namespace fcirc

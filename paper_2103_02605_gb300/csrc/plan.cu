@@ -32,6 +32,7 @@
 
 #include "../../include/fcirc_plan.h"
 #include "common.hpp"
+#include "kernels_mod.hpp"
 #include "ring.hpp"
 
 namespace fcirc {
@@ -330,6 +331,33 @@ static int build_plan(uint32_t p, uint32_t f, uint64_t n, Plan *pl)
         }
         FCIRC_TRY(upload((void **)&pl->d_ftw, ftw.data(), cnt * sizeof(Tw)));
         FCIRC_TRY(upload((void **)&pl->d_fitw, fitw.data(), cnt * sizeof(Tw)));
+        // group-ordered copies for the register-staged column passes: stage s
+        // of a pass over levels [l0, l1), group block gb (a node of level
+        // l0 + d0(s)), local level d, node j -> slot 16 gb + 16 - 2^(d+1) + j
+        std::vector<Tw> g, gi;
+        for (int i = 0; i < pl->npass; ++i) {
+            const int l0 = pl->pass_l0[i], lf = pl->pass_l1[i] - l0;
+            pl->pass_goff[i] = (int)g.size();
+            int off = 0;
+            for (int st = 0; st < col_nstage(lf); ++st) {
+                pl->stage_off[i][st] = off;
+                const int d0 = col_d0(lf, st), nl = col_nl(lf, st);
+                const uint64_t ngb = (uint64_t)1 << (l0 + d0);
+                g.resize(g.size() + ngb * 16, Tw{0, 0});
+                gi.resize(gi.size() + ngb * 16, Tw{0, 0});
+                Tw *G = g.data() + pl->pass_goff[i] + off, *GI = gi.data() + pl->pass_goff[i] + off;
+                for (uint64_t gb = 0; gb < ngb; ++gb)
+                    for (int d = 0; d < nl; ++d)
+                        for (uint64_t j = 0; j < ((uint64_t)1 << d); ++j) {
+                            const uint64_t heap = ((uint64_t)1 << (l0 + d0 + d)) + (gb << d) + j;
+                            G[gb * 16 + 16 - (2 << d) + j] = ftw[heap];
+                            GI[gb * 16 + 16 - (2 << d) + j] = fitw[heap];
+                        }
+                off += (int)(ngb * 16);
+            }
+        }
+        FCIRC_TRY(upload((void **)&pl->d_gtw, g.data(), g.size() * sizeof(Tw)));
+        FCIRC_TRY(upload((void **)&pl->d_gitw, gi.data(), gi.size() * sizeof(Tw)));
     }
     // ---- tile factors: rho_t = rho * Psi^brv_k(t), sigma_{t,d} = rho_t^(2^(D-1-d))
     {
@@ -367,6 +395,16 @@ static int build_plan(uint32_t p, uint32_t f, uint64_t n, Plan *pl)
     return FCIRC_OK;
 }
 
+static void free_plan_tables(Plan *pl)
+{
+    cudaFree(pl->d_ftw);
+    cudaFree(pl->d_fitw);
+    cudaFree(pl->d_sig);
+    cudaFree(pl->d_rho);
+    cudaFree(pl->d_gtw);
+    cudaFree(pl->d_gitw);
+}
+
 int get_plan(uint32_t p, uint32_t f, uint64_t n, const Plan **out)
 {
     int dev = 0;
@@ -382,10 +420,7 @@ int get_plan(uint32_t p, uint32_t f, uint64_t n, const Plan **out)
     Plan *pl = new Plan();
     int s = build_plan(p, f, n, pl);
     if (s != FCIRC_OK) {
-        cudaFree(pl->d_ftw);
-        cudaFree(pl->d_fitw);
-        cudaFree(pl->d_sig);
-        cudaFree(pl->d_rho);
+        free_plan_tables(pl);
         delete pl;
         return s;
     }
@@ -393,10 +428,7 @@ int get_plan(uint32_t p, uint32_t f, uint64_t n, const Plan **out)
     auto key = std::make_tuple(dev, p, f % p, n);
     auto it = g_plans.find(key);
     if (it != g_plans.end()) {  // built concurrently by another thread
-        cudaFree(pl->d_ftw);
-        cudaFree(pl->d_fitw);
-        cudaFree(pl->d_sig);
-        cudaFree(pl->d_rho);
+        free_plan_tables(pl);
         delete pl;
         *out = it->second;
         return FCIRC_OK;
@@ -413,10 +445,7 @@ void release_plans()
         cudaSetDevice(std::get<0>(kv.first));
         cudaDeviceSynchronize();
         Plan *pl = kv.second;
-        cudaFree(pl->d_ftw);
-        cudaFree(pl->d_fitw);
-        cudaFree(pl->d_sig);
-        cudaFree(pl->d_rho);
+        free_plan_tables(pl);
         delete pl;
     }
     g_plans.clear();
