@@ -73,6 +73,34 @@ int fcirc_matvec(uint32_t p, uint32_t f, const uint32_t *a, const uint32_t *x,
                  uint32_t *c, uint64_t n, void *stream);
 
 /*
+ * fcirc_matvec_noalloc -- the same product as fcirc_matvec for callers that
+ * cannot let the library allocate device memory (a process that reserved
+ * its GPU memory in fixed pools up front, or that must not see the
+ * device-wide synchronisation an allocation can cause while its streams
+ * run).  The paper has no counterpart; this is an interface variant only.
+ *
+ * Arguments and results are those of fcirc_matvec, with three limits:
+ *   * a, x, c must be device pointers on the current device (FCIRC_EINVAL
+ *     otherwise: host buffers would need staging memory);
+ *   * 2 <= n <= 2^20 (FCIRC_EINVAL beyond, with a message naming the limit);
+ *   * the call never allocates: its scratch (the vector side's intermediate)
+ *     and its plan tables live in one 5 MiB array inside the library that
+ *     every GPU loading the library holds until the process exits.
+ *
+ * All calls on a device share that array, and it keeps the last call's
+ * tables and intermediate: calls whose work overlaps on the GPU (two streams,
+ * or two host threads) race with each other and must be serialised by the
+ * caller.  A call for a new (p, f, n) writes its tables with a host-to-device
+ * copy on `stream` before its kernels; nothing else needs clearing, since
+ * every scratch word is written before it is read.  The first call on each
+ * device also looks up the array's device address (once per device, with
+ * that device current); make that first call before capturing any stream
+ * into a CUDA graph.
+ */
+int fcirc_matvec_noalloc(uint32_t p, uint32_t f, const uint32_t *a, const uint32_t *x,
+                         uint32_t *c, uint64_t n, void *stream);
+
+/*
  * poly_mul_int -- exact product of two polynomials with 16-bit unsigned
  * integer coefficients (Section 3.1): out[k] = sum_{i+j=k} P[i] Q[j] for
  * k < np + nq - 1.

@@ -20,7 +20,7 @@ from . import build as _build
 
 __all__ = [
     "FcircError", "library_path", "load",
-    "fcirc_matvec", "poly_mul_int", "sync_status", "release",
+    "fcirc_matvec", "fcirc_matvec_noalloc", "poly_mul_int", "sync_status", "release",
     "nth_root", "node_twiddle", "leaf_param", "twiddle_from_factor",
     "prof_start", "prof_stop", "prof_report", "prof_launches",
     "PRIMES",
@@ -36,6 +36,7 @@ _vp = ctypes.c_void_p
 
 _SIGNATURES = {
     "fcirc_matvec": ([_u32, _u32, _vp, _vp, _vp, _u64, _vp], _i32),
+    "fcirc_matvec_noalloc": ([_u32, _u32, _vp, _vp, _vp, _u64, _vp], _i32),
     "poly_mul_int": ([_vp, _u64, _vp, _u64, _vp, _vp], _i32),
     "fcirc_sync_status": ([_vp], _i32),
     "fcirc_error_string": ([_i32], ctypes.c_char_p),
@@ -124,6 +125,21 @@ def fcirc_matvec(p: int, f: int, a, x, out=None, stream=None):
     st = _stream_handle(stream, a, x, out)
     _check(load().fcirc_matvec(p, f % p, a.data_ptr(), x.data_ptr(), out.data_ptr(), a.numel(), st),
            "fcirc_matvec")
+    return out
+
+
+def fcirc_matvec_noalloc(p: int, f: int, a, x, out, stream=None):
+    """fcirc_matvec for callers that cannot let the library allocate: a, x and
+    out are device tensors (out preallocated), n <= 2^20; the library works
+    in a fixed array it holds from load time (see include/fcirc.h)."""
+    _u32_tensor(a, "a")
+    _u32_tensor(x, "x")
+    _u32_tensor(out, "out")
+    if a.shape != x.shape or a.shape != out.shape or a.dim() != 1:
+        raise ValueError("a, x and out must be 1-D of the same length")
+    st = _stream_handle(stream, a, x, out)
+    _check(load().fcirc_matvec_noalloc(p, f % p, a.data_ptr(), x.data_ptr(), out.data_ptr(), a.numel(), st),
+           "fcirc_matvec_noalloc")
     return out
 
 
