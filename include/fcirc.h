@@ -121,6 +121,24 @@ int poly_mul_int(const uint16_t *P, uint64_t np, const uint16_t *Q,
                  uint64_t nq, int64_t *out, void *stream);
 
 /*
+ * bigint_mul -- product of two unsigned integers given as little-endian
+ * base-2^16 limbs (Section 3.2: the integers are split into parts that are
+ * read as polynomial coefficients, the polynomials are multiplied through
+ * the circulant product, and the carries are propagated).
+ *
+ *   A    na limbs (uint16, least significant first), B  nb limbs;
+ *        1 <= na, nb and na + nb - 1 <= 2^24.
+ *   out  na + nb limbs of A * B (the top limb may be zero).
+ *
+ * The column sums come from the same three-prime circulant products and CRT
+ * as poly_mul_int; the carries are resolved by a parallel carry-lookahead
+ * (three launches, no device-side waiting).
+ * Errors: FCIRC_EINVAL for null pointers, zero or too large sizes.
+ */
+int bigint_mul(const uint16_t *A, uint64_t na, const uint16_t *B, uint64_t nb,
+               uint16_t *out, void *stream);
+
+/*
  * fcirc_sync_status -- waits for `stream`, then returns and clears the
  * library's sticky device status word for the current device: FCIRC_OK, or
  * FCIRC_ETIMEOUT if a bounded device-side wait gave up since the last call,

@@ -20,7 +20,7 @@ from . import build as _build
 
 __all__ = [
     "FcircError", "library_path", "load",
-    "fcirc_matvec", "fcirc_matvec_noalloc", "poly_mul_int", "sync_status", "release",
+    "fcirc_matvec", "fcirc_matvec_noalloc", "poly_mul_int", "bigint_mul", "sync_status", "release",
     "nth_root", "node_twiddle", "leaf_param", "twiddle_from_factor",
     "prof_start", "prof_stop", "prof_report", "prof_launches",
     "PRIMES",
@@ -38,6 +38,7 @@ _SIGNATURES = {
     "fcirc_matvec": ([_u32, _u32, _vp, _vp, _vp, _u64, _vp], _i32),
     "fcirc_matvec_noalloc": ([_u32, _u32, _vp, _vp, _vp, _u64, _vp], _i32),
     "poly_mul_int": ([_vp, _u64, _vp, _u64, _vp, _vp], _i32),
+    "bigint_mul": ([_vp, _u64, _vp, _u64, _vp, _vp], _i32),
     "fcirc_sync_status": ([_vp], _i32),
     "fcirc_error_string": ([_i32], ctypes.c_char_p),
     "fcirc_last_error": ([], ctypes.c_char_p),
@@ -159,6 +160,24 @@ def poly_mul_int(P, Q, out=None, stream=None):
     st = _stream_handle(stream, P, Q, out)
     _check(load().poly_mul_int(P.data_ptr(), P.numel(), Q.data_ptr(), Q.numel(), out.data_ptr(), st),
            "poly_mul_int")
+    return out
+
+
+def bigint_mul(A, B, out=None, stream=None):
+    """Product of two unsigned integers given as little-endian 16-bit limbs
+    (Section 3.2).  A, B: 1-D int16/uint16 tensors; returns len(A) + len(B)
+    limbs (int16 tensor holding the uint16 bit patterns)."""
+    import torch
+    for t, nm in ((A, "A"), (B, "B")):
+        if t.dtype not in (torch.int16, getattr(torch, "uint16", torch.int16)):
+            raise TypeError(f"{nm} must be a 16-bit tensor, got {t.dtype}")
+        if not t.is_contiguous() or t.dim() != 1:
+            raise ValueError(f"{nm} must be 1-D contiguous")
+    if out is None:
+        out = torch.empty(A.numel() + B.numel(), dtype=torch.int16, device=A.device)
+    st = _stream_handle(stream, A, B, out)
+    _check(load().bigint_mul(A.data_ptr(), A.numel(), B.data_ptr(), B.numel(), out.data_ptr(), st),
+           "bigint_mul")
     return out
 
 

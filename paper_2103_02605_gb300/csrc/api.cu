@@ -6,6 +6,7 @@
 #include <vector>
 
 #include "common.hpp"
+#include "kernels_bigint.hpp"
 #include "kernels_mod.hpp"
 #include "ring.hpp"
 
@@ -401,6 +402,37 @@ int poly_mul_int(const uint16_t *P, uint64_t np, const uint16_t *Q, uint64_t nq,
     FCIRC_TRY(st.begin(s, poly_scratch_bytes(N)));
     FCIRC_TRY(poly_core(static_cast<const uint16_t *>(aP.d), np, static_cast<const uint16_t *>(aQ.d), nq,
                         static_cast<uint64_t *>(aO.d), nout, N, st.scratch, s));
+    return st.end();
+}
+
+int bigint_mul(const uint16_t *A, uint64_t na, const uint16_t *B, uint64_t nb, uint16_t *out, void *stream)
+{
+    set_error("");
+    if (!A || !B || !out) return fail(FCIRC_EINVAL, "bigint_mul: null pointer");
+    if (na == 0 || nb == 0) return fail(FCIRC_EINVAL, "bigint_mul: empty operand");
+    const uint64_t ncols = na + nb - 1, nlimbs = na + nb;
+    if (ncols > ((uint64_t)1 << 24))
+        return fail(FCIRC_EINVAL, "bigint_mul: na + nb - 1 = %llu exceeds 2^24 limbs", (unsigned long long)ncols);
+    uint64_t N = 2;
+    while (N < ncols) N <<= 1;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    for (int q = 0; q < 3; ++q) {
+        const Plan *pl;
+        FCIRC_TRY(get_plan(kPrimes[q], 1, N, &pl));
+    }
+    Arg aA{A, na * 2, true, false}, aB{B, nb * 2, true, false}, aO{out, nlimbs * 2, false, true};
+    Staging st;
+    st.args = {&aA, &aB, &aO};
+    // scratch: the polynomial pipeline, the 64-bit column sums, the carry maps
+    const size_t pb = (poly_scratch_bytes(N) + 255) & ~(size_t)255;
+    const size_t cb = (ncols * 8 + 255) & ~(size_t)255;
+    FCIRC_TRY(st.begin(s, pb + cb + carry_scratch_bytes(nlimbs)));
+    uint64_t *cols = reinterpret_cast<uint64_t *>(st.scratch + pb);
+    // column sums sum_{i+j=k} A_i B_j: the polynomial product of the limb
+    // vectors (Section 3.2: the parts as polynomial coefficients)
+    FCIRC_TRY(poly_core(static_cast<const uint16_t *>(aA.d), na, static_cast<const uint16_t *>(aB.d), nb, cols,
+                        ncols, N, st.scratch, s));
+    FCIRC_TRY(launch_carry(cols, ncols, static_cast<uint16_t *>(aO.d), nlimbs, st.scratch + pb + cb, s));
     return st.end();
 }
 
