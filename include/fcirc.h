@@ -139,6 +139,43 @@ int bigint_mul(const uint16_t *A, uint64_t na, const uint16_t *B, uint64_t nb,
                uint16_t *out, void *stream);
 
 /*
+ * fcirc_matvec_c64 -- c = A x for a batch of complex f-circulant products in
+ * FP32 (Definition 2's layout; the same recursion as fcirc_matvec, Algorithm
+ * 1, over the complex numbers as the closing remark of Section 3.1 notes
+ * real or complex coefficients need).  Roots and twiddles are formed in FP64
+ * and rounded to FP32.
+ *
+ *   a, x, c  batch instances of n complex numbers, each an interleaved
+ *            (re, im) float pair; instance b at offset 2 n b floats.
+ *   f        the parameter, f_re + i f_im != 0 (the same for every instance).
+ *   n        a power of two, 8 <= n <= 4096;  batch >= 0.
+ *
+ * Accuracy: relative L2 error of order 1e-7 log2(n) against exact arithmetic
+ * for |f| = 1 and inputs of comparable magnitude.
+ * Errors: FCIRC_EINVAL for null pointers or an unsupported n, FCIRC_ENOROOT
+ * for f = 0.
+ */
+int fcirc_matvec_c64(const float *a, const float *x, float *c, double f_re, double f_im,
+                     uint64_t n, uint64_t batch, void *stream);
+
+/*
+ * fcirc_matvec_backward -- gradients of the real loss L = Re <g, A x> (the
+ * convention PyTorch uses for complex tensors: the gradient of z is
+ * dL/dRe z + i dL/dIm z), for the same batch layout as fcirc_matvec_c64:
+ *
+ *   grad_x = A^H g = the (1/conj f)-circulant with row
+ *            (conj a_0, conj(f) conj a_{n-1}, ..., conj(f) conj a_1), times g;
+ *   grad_a = the conj(f)-circulant with row g, times conj(x).
+ *
+ * Both are computed with the same halving recursion (two more f'-circulant
+ * products), in one pass over a, x and g.  The paper does not treat
+ * gradients; they follow from Definition 2 by differentiation.
+ * Errors: as fcirc_matvec_c64.
+ */
+int fcirc_matvec_backward(const float *a, const float *x, const float *g, double f_re, double f_im,
+                          float *grad_a, float *grad_x, uint64_t n, uint64_t batch, void *stream);
+
+/*
  * fcirc_sync_status -- waits for `stream`, then returns and clears the
  * library's sticky device status word for the current device: FCIRC_OK, or
  * FCIRC_ETIMEOUT if a bounded device-side wait gave up since the last call,

@@ -20,7 +20,8 @@ from . import build as _build
 
 __all__ = [
     "FcircError", "library_path", "load",
-    "fcirc_matvec", "fcirc_matvec_noalloc", "poly_mul_int", "bigint_mul", "sync_status", "release",
+    "fcirc_matvec", "fcirc_matvec_noalloc", "poly_mul_int", "bigint_mul",
+    "fcirc_matvec_c64", "fcirc_matvec_backward", "fcirc_layer", "sync_status", "release",
     "nth_root", "node_twiddle", "leaf_param", "twiddle_from_factor",
     "prof_start", "prof_stop", "prof_report", "prof_launches",
     "PRIMES",
@@ -39,6 +40,9 @@ _SIGNATURES = {
     "fcirc_matvec_noalloc": ([_u32, _u32, _vp, _vp, _vp, _u64, _vp], _i32),
     "poly_mul_int": ([_vp, _u64, _vp, _u64, _vp, _vp], _i32),
     "bigint_mul": ([_vp, _u64, _vp, _u64, _vp, _vp], _i32),
+    "fcirc_matvec_c64": ([_vp, _vp, _vp, ctypes.c_double, ctypes.c_double, _u64, _u64, _vp], _i32),
+    "fcirc_matvec_backward": ([_vp, _vp, _vp, ctypes.c_double, ctypes.c_double, _vp, _vp, _u64, _u64, _vp],
+                              _i32),
     "fcirc_sync_status": ([_vp], _i32),
     "fcirc_error_string": ([_i32], ctypes.c_char_p),
     "fcirc_last_error": ([], ctypes.c_char_p),
@@ -179,6 +183,82 @@ def bigint_mul(A, B, out=None, stream=None):
     _check(load().bigint_mul(A.data_ptr(), A.numel(), B.data_ptr(), B.numel(), out.data_ptr(), st),
            "bigint_mul")
     return out
+
+
+def _c64(t, name):
+    import torch
+    if t.dtype != torch.complex64 or not t.is_contiguous():
+        raise TypeError(f"{name} must be a contiguous complex64 tensor")
+    return t
+
+
+def fcirc_matvec_c64(a, x, f=1.0, out=None, stream=None):
+    """Batched complex f-circulant product c = A x in FP32; a, x of shape
+    (batch, n) or (n,), complex64."""
+    import torch
+    _c64(a, "a")
+    _c64(x, "x")
+    if a.shape != x.shape:
+        raise ValueError("a and x must have the same shape")
+    n = a.shape[-1]
+    batch = a.numel() // n if n else 0
+    if out is None:
+        out = torch.empty_like(a)
+    _c64(out, "out")
+    f = complex(f)
+    st = _stream_handle(stream, a, x, out)
+    _check(load().fcirc_matvec_c64(a.data_ptr(), x.data_ptr(), out.data_ptr(), f.real, f.imag, n, batch, st),
+           "fcirc_matvec_c64")
+    return out
+
+
+def fcirc_matvec_backward(a, x, g, f=1.0, stream=None):
+    """(grad_a, grad_x) of Re <g, A x> (PyTorch's complex convention)."""
+    import torch
+    for t, nm in ((a, "a"), (x, "x"), (g, "g")):
+        _c64(t, nm)
+    n = a.shape[-1]
+    batch = a.numel() // n if n else 0
+    ga = torch.empty_like(a)
+    gx = torch.empty_like(x)
+    f = complex(f)
+    st = _stream_handle(stream, a, x, g)
+    _check(load().fcirc_matvec_backward(a.data_ptr(), x.data_ptr(), g.data_ptr(), f.real, f.imag,
+                                        ga.data_ptr(), gx.data_ptr(), n, batch, st), "fcirc_matvec_backward")
+    return ga, gx
+
+
+def _autograd_fn():
+    import torch
+
+    class FCircC64(torch.autograd.Function):
+        """c = A x for f-circulant A with row vector a (complex FP32), with the
+        hand-written adjoint as backward (see fcirc_matvec_backward)."""
+
+        @staticmethod
+        def forward(ctx, a, x, f):
+            ctx.save_for_backward(a, x)
+            ctx.f = f
+            return fcirc_matvec_c64(a.contiguous(), x.contiguous(), f)
+
+        @staticmethod
+        def backward(ctx, g):
+            a, x = ctx.saved_tensors
+            ga, gx = fcirc_matvec_backward(a.contiguous(), x.contiguous(), g.contiguous(), ctx.f)
+            return ga, gx, None
+
+    return FCircC64
+
+
+_FCIRC_FN = None
+
+
+def fcirc_layer(a, x, f=1.0):
+    """Differentiable complex f-circulant product (torch.autograd.Function)."""
+    global _FCIRC_FN
+    if _FCIRC_FN is None:
+        _FCIRC_FN = _autograd_fn()
+    return _FCIRC_FN.apply(a, x, complex(f))
 
 
 def sync_status(stream=None) -> int:

@@ -3,10 +3,13 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <cmath>
+
 #include <vector>
 
 #include "common.hpp"
 #include "kernels_bigint.hpp"
+#include "kernels_complex.hpp"
 #include "kernels_mod.hpp"
 #include "ring.hpp"
 
@@ -436,6 +439,70 @@ int bigint_mul(const uint16_t *A, uint64_t na, const uint16_t *B, uint64_t nb, u
     return st.end();
 }
 
+int fcirc_matvec_c64(const float *a, const float *x, float *c, double f_re, double f_im, uint64_t n,
+                     uint64_t batch, void *stream)
+{
+    set_error("");
+    if (!a || !x || !c) return fail(FCIRC_EINVAL, "fcirc_matvec_c64: null pointer");
+    if (!is_pow2(n) || n < 8 || n > 4096)
+        return fail(FCIRC_EINVAL, "fcirc_matvec_c64: n = %llu must be a power of two in [8, 4096]",
+                    (unsigned long long)n);
+    if (f_re == 0.0 && f_im == 0.0) return fail(FCIRC_ENOROOT, "fcirc_matvec_c64: f = 0 has no inverse");
+    if (batch == 0) return FCIRC_OK;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const int m = ilog2(n);
+    CParams P{};
+    FCIRC_TRY(complex_tables(f_re, f_im, n, &P.tw, &P.itw));
+    const size_t bytes = n * batch * 8;
+    Arg aa{a, bytes, true, false}, ax{x, bytes, true, false}, ac{c, bytes, false, true};
+    Staging st;
+    st.args = {&aa, &ax, &ac};
+    FCIRC_TRY(st.begin(s, 0));
+    P.a = static_cast<const float *>(aa.d);
+    P.x = static_cast<const float *>(ax.d);
+    P.c = static_cast<float *>(ac.d);
+    P.batch = batch;
+    P.scale = std::ldexp(1.0f, -(m - 1));
+    FCIRC_TRY(launch_cfwd(P, m, s));
+    return st.end();
+}
+
+int fcirc_matvec_backward(const float *a, const float *x, const float *g, double f_re, double f_im,
+                          float *grad_a, float *grad_x, uint64_t n, uint64_t batch, void *stream)
+{
+    set_error("");
+    if (!a || !x || !g || !grad_a || !grad_x) return fail(FCIRC_EINVAL, "fcirc_matvec_backward: null pointer");
+    if (!is_pow2(n) || n < 8 || n > 4096)
+        return fail(FCIRC_EINVAL, "fcirc_matvec_backward: n = %llu must be a power of two in [8, 4096]",
+                    (unsigned long long)n);
+    const double f2 = f_re * f_re + f_im * f_im;
+    if (f2 == 0.0) return fail(FCIRC_ENOROOT, "fcirc_matvec_backward: f = 0 has no inverse");
+    if (batch == 0) return FCIRC_OK;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const int m = ilog2(n);
+    CBwdParams P{};
+    // dL/dx: parameter 1/conj(f) = f / |f|^2; dL/da: parameter conj(f)
+    FCIRC_TRY(complex_tables(f_re / f2, f_im / f2, n, &P.tw_x, &P.itw_x));
+    FCIRC_TRY(complex_tables(f_re, -f_im, n, &P.tw_a, &P.itw_a));
+    const size_t bytes = n * batch * 8;
+    Arg aa{a, bytes, true, false}, ax{x, bytes, true, false}, ag{g, bytes, true, false};
+    Arg oa{grad_a, bytes, false, true}, ox{grad_x, bytes, false, true};
+    Staging st;
+    st.args = {&aa, &ax, &ag, &oa, &ox};
+    FCIRC_TRY(st.begin(s, 0));
+    P.a = static_cast<const float *>(aa.d);
+    P.x = static_cast<const float *>(ax.d);
+    P.g = static_cast<const float *>(ag.d);
+    P.grad_a = static_cast<float *>(oa.d);
+    P.grad_x = static_cast<float *>(ox.d);
+    P.fc_re = (float)f_re;
+    P.fc_im = (float)(-f_im);
+    P.batch = batch;
+    P.scale = std::ldexp(1.0f, -(m - 1));
+    FCIRC_TRY(launch_cbwd(P, m, s));
+    return st.end();
+}
+
 int fcirc_sync_status(void *stream)
 {
     set_error("");
@@ -457,6 +524,7 @@ int fcirc_release(void)
     set_error("");
     release_scratch();
     release_plans();
+    release_cplans();
     return FCIRC_OK;
 }
 

@@ -1,0 +1,449 @@
+// kernels_complex.cu -- the f-circulant product over complex numbers in
+// FP32 (the closing remark of Section 3.1: real or complex coefficients need
+// complex roots), forward and hand-written backward, batched.
+//
+// Same recursion as the modular path (Algorithm 1): row-vector butterflies
+// lo +- s hi, vector butterflies s lo +- hi, 2x2 leaves, recombination
+// ((M1 + M2) s^-1, M1 - M2) with the halvings deferred to one exact scaling
+// by 2^-L at the end.  Twiddles s_{l,j} = |f|^(1/2^(l+1)) exp(i (arg f +
+// 2 pi brv_l(j)) / 2^(l+1)) are formed in FP64 on the host and rounded to
+// FP32.
+//
+// Backward, for L = Re <g, A x> (PyTorch's convention for complex tensors):
+//   dL/dx = A^H g = RowCirc_{1/conj(f)}(beta) g,
+//           beta = (conj a_0, conj(f) conj a_{n-1}, ..., conj(f) conj a_1),
+//   dL/da = RowCirc_{conj(f)}(g) conj(x),
+// two more f'-circulant products through the same recursion, computed
+// together in one CTA per instance.
+//
+// Layout: n = 2^M complex numbers per instance, interleaved (re, im) float,
+// instances back to back.  A thread owns 8 numbers of a side; the CTA runs
+// register stages of up to 3 levels with shared-memory exchanges, the last
+// stage on 8 contiguous numbers (bottom two levels, four 2x2 leaves, and
+// the first two recombination levels).
+#include <cmath>
+#include <map>
+#include <mutex>
+#include <tuple>
+#include <vector>
+
+#include "common.hpp"
+#include "kernels_complex.hpp"
+#include "prof.hpp"
+#include "ring.hpp"
+
+namespace fcirc {
+
+namespace {
+
+__device__ __forceinline__ float2 cmul(float2 a, float2 b)
+{
+    return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
+}
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float2 cconj(float2 a) { return make_float2(a.x, -a.y); }
+__device__ __forceinline__ float2 cneg(float2 a) { return make_float2(-a.x, -a.y); }
+
+template <int M>
+struct CShape {
+    static constexpr int N = 1 << M;
+    static constexpr int L = M - 1;           // halving levels; 2x2 leaves below
+    static constexpr int NTI = N / 8;         // threads per instance
+    static constexpr int CT = NTI < 128 ? 128 : NTI;   // threads per CTA
+    static constexpr int IPC = CT / NTI;      // instances per CTA
+    static constexpr int P = L - 2;           // levels before the last stage
+    static constexpr int NST = (P + 2) / 3;   // stages of up to 3 levels, remainder first
+    static constexpr int nl(int s) { return s == 0 ? P - 3 * (NST - 1) : 3; }
+    static constexpr int d0(int s) { return s == 0 ? 0 : (P - 3 * (NST - 1)) + 3 * (s - 1); }
+};
+
+// One product's data in shared memory: row-vector side R and vector side X.
+struct Side {
+    float2 *R, *X;
+    const float2 *tw, *itw;   // heap-indexed twiddles and inverses, [N/2]
+};
+
+// forward stage S (levels d0 .. d0+nl-1) on both sides
+template <int M, int S>
+__device__ __forceinline__ void cfwd_stage(Side &sd, int t)
+{
+    using Sh = CShape<M>;
+    constexpr int NL = Sh::nl(S), D0 = Sh::d0(S), G = 8 >> NL, MM = 1 << NL;
+    constexpr int LST = M - D0 - NL, LRB = M - D0;
+#pragma unroll
+    for (int h = 0; h < G; ++h) {
+        const int gg = t + Sh::NTI * h;
+        const int blk = gg >> LST, off = gg & ((1 << LST) - 1);
+        const int e0 = (blk << LRB) + off;
+        float2 r[MM], x[MM];
+#pragma unroll
+        for (int i = 0; i < MM; ++i) {
+            r[i] = sd.R[e0 + (i << LST)];
+            x[i] = sd.X[e0 + (i << LST)];
+        }
+#pragma unroll
+        for (int d = 0; d < NL; ++d) {
+            const int hh = MM >> (d + 1);
+#pragma unroll
+            for (int j = 0; j < (1 << d); ++j) {
+                const float2 s = __ldg(&sd.tw[(1 << (D0 + d)) + (blk << d) + j]);
+#pragma unroll
+                for (int i = 0; i < hh; ++i) {
+                    const int lo = (j << (NL - d)) + i, hi = lo + hh;
+                    const float2 tr = cmul(s, r[hi]);
+                    const float2 tx = cmul(s, x[lo]);
+                    r[hi] = csub(r[lo], tr);
+                    r[lo] = cadd(r[lo], tr);
+                    const float2 xh = x[hi];
+                    x[hi] = csub(tx, xh);
+                    x[lo] = cadd(tx, xh);
+                }
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < MM; ++i) {
+            sd.R[e0 + (i << LST)] = r[i];
+            sd.X[e0 + (i << LST)] = x[i];
+        }
+    }
+}
+
+// recombination stage S (levels d0+nl-1 .. d0), result in R
+template <int M, int S>
+__device__ __forceinline__ void crec_stage(Side &sd, int t)
+{
+    using Sh = CShape<M>;
+    constexpr int NL = Sh::nl(S), D0 = Sh::d0(S), G = 8 >> NL, MM = 1 << NL;
+    constexpr int LST = M - D0 - NL, LRB = M - D0;
+#pragma unroll
+    for (int h = 0; h < G; ++h) {
+        const int gg = t + Sh::NTI * h;
+        const int blk = gg >> LST, off = gg & ((1 << LST) - 1);
+        const int e0 = (blk << LRB) + off;
+        float2 r[MM];
+#pragma unroll
+        for (int i = 0; i < MM; ++i) r[i] = sd.R[e0 + (i << LST)];
+#pragma unroll
+        for (int d = NL - 1; d >= 0; --d) {
+            const int hh = MM >> (d + 1);
+#pragma unroll
+            for (int j = 0; j < (1 << d); ++j) {
+                const float2 si = __ldg(&sd.itw[(1 << (D0 + d)) + (blk << d) + j]);
+#pragma unroll
+                for (int i = 0; i < hh; ++i) {
+                    const int lo = (j << (NL - d)) + i, hi = lo + hh;
+                    const float2 sum = cadd(r[lo], r[hi]);
+                    r[hi] = csub(r[lo], r[hi]);
+                    r[lo] = cmul(sum, si);
+                }
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < MM; ++i) sd.R[e0 + (i << LST)] = r[i];
+    }
+}
+
+// last stage: 8 contiguous numbers at 8t: levels L-2, L-1, four 2x2
+// leaves, recombination L-1, L-2; result in R
+template <int M>
+__device__ __forceinline__ void cleaf_stage(Side &sd, int t)
+{
+    constexpr int L = M - 1;
+    float2 r[8], x[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        r[i] = sd.R[8 * t + i];
+        x[i] = sd.X[8 * t + i];
+    }
+    const float2 s0 = __ldg(&sd.tw[(1 << (L - 2)) + t]);
+    const float2 s1[2] = {__ldg(&sd.tw[(1 << (L - 1)) + 2 * t]), __ldg(&sd.tw[(1 << (L - 1)) + 2 * t + 1])};
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const float2 tr = cmul(s0, r[i + 4]), tx = cmul(s0, x[i]);
+        r[i + 4] = csub(r[i], tr);
+        r[i] = cadd(r[i], tr);
+        const float2 xh = x[i + 4];
+        x[i + 4] = csub(tx, xh);
+        x[i] = cadd(tx, xh);
+    }
+#pragma unroll
+    for (int hb = 0; hb < 2; ++hb)
+#pragma unroll
+        for (int i = 0; i < 2; ++i) {
+            const int lo = 4 * hb + i, hi = lo + 2;
+            const float2 tr = cmul(s1[hb], r[hi]), tx = cmul(s1[hb], x[lo]);
+            r[hi] = csub(r[lo], tr);
+            r[lo] = cadd(r[lo], tr);
+            const float2 xh = x[hi];
+            x[hi] = csub(tx, xh);
+            x[lo] = cadd(tx, xh);
+        }
+    // leaves (2q, 2q+1): the phi-circulant [[a0, a1], [phi a1, a0]], phi = +-s_{L-1}
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const float2 phi = (q & 1) ? cneg(s1[q >> 1]) : s1[q >> 1];
+        const float2 a0 = r[2 * q], a1 = r[2 * q + 1], y0 = x[2 * q], y1 = x[2 * q + 1];
+        const float2 a1f = cmul(phi, a1);
+        r[2 * q] = cadd(cmul(a0, y0), cmul(a1, y1));
+        r[2 * q + 1] = cadd(cmul(a1f, y0), cmul(a0, y1));
+    }
+    const float2 i1[2] = {__ldg(&sd.itw[(1 << (L - 1)) + 2 * t]), __ldg(&sd.itw[(1 << (L - 1)) + 2 * t + 1])};
+    const float2 i0 = __ldg(&sd.itw[(1 << (L - 2)) + t]);
+#pragma unroll
+    for (int hb = 0; hb < 2; ++hb)
+#pragma unroll
+        for (int i = 0; i < 2; ++i) {
+            const int lo = 4 * hb + i, hi = lo + 2;
+            const float2 sum = cadd(r[lo], r[hi]);
+            r[hi] = csub(r[lo], r[hi]);
+            r[lo] = cmul(sum, i1[hb]);
+        }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const float2 sum = cadd(r[i], r[i + 4]);
+        r[i + 4] = csub(r[i], r[i + 4]);
+        r[i] = cmul(sum, i0);
+    }
+#pragma unroll
+    for (int i = 0; i < 8; ++i) sd.R[8 * t + i] = r[i];
+}
+
+// whole product for one instance: forward stages, last stage, recombination
+template <int M, int S>
+__device__ __forceinline__ void cfwd_all(Side &sd, int t)
+{
+    if constexpr (S < CShape<M>::NST) {
+        cfwd_stage<M, S>(sd, t);
+        __syncthreads();
+        cfwd_all<M, S + 1>(sd, t);
+    }
+}
+
+template <int M, int S>
+__device__ __forceinline__ void crec_all(Side &sd, int t)
+{
+    if constexpr (S >= 0) {
+        crec_stage<M, S>(sd, t);
+        __syncthreads();
+        crec_all<M, S - 1>(sd, t);
+    }
+}
+
+template <int M>
+__device__ __forceinline__ void cproduct(Side &sd, int t)
+{
+    cfwd_all<M, 0>(sd, t);
+    cleaf_stage<M>(sd, t);
+    __syncthreads();
+    crec_all<M, CShape<M>::NST - 1>(sd, t);
+}
+
+template <int M>
+__global__ void __launch_bounds__(CShape<M>::CT) k_cfwd(const __grid_constant__ CParams P)
+{
+    using Sh = CShape<M>;
+    extern __shared__ __align__(16) float2 csm[];
+    const int li = threadIdx.x / Sh::NTI, t = threadIdx.x % Sh::NTI;
+    const uint64_t inst = (uint64_t)blockIdx.x * Sh::IPC + li;
+    const bool live = inst < P.batch;
+    Side sd{csm + (size_t)li * 2 * Sh::N, csm + (size_t)li * 2 * Sh::N + Sh::N, P.tw, P.itw};
+    const float2 *a = reinterpret_cast<const float2 *>(P.a) + inst * Sh::N;
+    const float2 *x = reinterpret_cast<const float2 *>(P.x) + inst * Sh::N;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        const int e = t + Sh::NTI * k;
+        sd.R[e] = live ? a[e] : make_float2(0.f, 0.f);
+        sd.X[e] = live ? x[e] : make_float2(0.f, 0.f);
+    }
+    __syncthreads();
+    cproduct<M>(sd, t);
+    if (live) {
+        float2 *c = reinterpret_cast<float2 *>(P.c) + inst * Sh::N;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            const int e = t + Sh::NTI * k;
+            const float2 v = sd.R[e];
+            c[e] = make_float2(v.x * P.scale, v.y * P.scale);
+        }
+    }
+}
+
+// dL/dx and dL/da of one instance per Sh::NTI threads
+template <int M>
+__global__ void __launch_bounds__(CShape<M>::CT) k_cbwd(const __grid_constant__ CBwdParams P)
+{
+    using Sh = CShape<M>;
+    extern __shared__ __align__(16) float2 csm[];
+    const int li = threadIdx.x / Sh::NTI, t = threadIdx.x % Sh::NTI;
+    const uint64_t inst = (uint64_t)blockIdx.x * Sh::IPC + li;
+    const bool live = inst < P.batch;
+    float2 *base = csm + (size_t)li * 4 * Sh::N;
+    Side sx{base, base + Sh::N, P.tw_x, P.itw_x};                // beta(a) and g
+    Side sa{base + 2 * Sh::N, base + 3 * Sh::N, P.tw_a, P.itw_a};  // g and conj(x)
+    const float2 *a = reinterpret_cast<const float2 *>(P.a) + inst * Sh::N;
+    const float2 *x = reinterpret_cast<const float2 *>(P.x) + inst * Sh::N;
+    const float2 *g = reinterpret_cast<const float2 *>(P.g) + inst * Sh::N;
+    const float2 fc = make_float2(P.fc_re, P.fc_im);   // conj(f)
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        const int e = t + Sh::NTI * k;
+        const float2 z = make_float2(0.f, 0.f);
+        // beta_e = conj(a_0) for e = 0, conj(f) conj(a_{n-e}) otherwise
+        const float2 ae = live ? a[e == 0 ? 0 : Sh::N - e] : z;
+        sx.R[e] = e == 0 ? cconj(ae) : cmul(fc, cconj(ae));
+        const float2 ge = live ? g[e] : z;
+        sx.X[e] = ge;
+        sa.R[e] = ge;
+        sa.X[e] = live ? cconj(x[e]) : z;
+    }
+    __syncthreads();
+    cproduct<M>(sx, t);
+    cproduct<M>(sa, t);
+    if (live) {
+        float2 *gx = reinterpret_cast<float2 *>(P.grad_x) + inst * Sh::N;
+        float2 *ga = reinterpret_cast<float2 *>(P.grad_a) + inst * Sh::N;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            const int e = t + Sh::NTI * k;
+            const float2 vx = sx.R[e], va = sa.R[e];
+            gx[e] = make_float2(vx.x * P.scale, vx.y * P.scale);
+            ga[e] = make_float2(va.x * P.scale, va.y * P.scale);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// host: twiddle tables per (f, n), FP64 -> FP32
+
+struct CPlanKey {
+    int dev;
+    double re, im;
+    uint64_t n;
+    bool operator<(const CPlanKey &o) const { return std::tie(dev, re, im, n) < std::tie(o.dev, o.re, o.im, o.n); }
+};
+std::mutex g_cmu;
+std::map<CPlanKey, std::pair<float2 *, float2 *>> g_cplans;
+
+int get_ctables(double fre, double fim, uint64_t n, const float2 **tw, const float2 **itw)
+{
+    int dev = 0;
+    FCIRC_CUDA_TRY(cudaGetDevice(&dev));
+    const CPlanKey key{dev, fre, fim, n};
+    std::lock_guard<std::mutex> lk(g_cmu);
+    auto it = g_cplans.find(key);
+    if (it == g_cplans.end()) {
+        const int m = ilog2(n), L = m - 1;
+        const double r = std::hypot(fre, fim), th = std::atan2(fim, fre);
+        std::vector<float2> h(n / 2), hi(n / 2);
+        h[0] = hi[0] = make_float2(0.f, 0.f);
+        for (int l = 0; l < L; ++l) {
+            const double mag = std::pow(r, std::ldexp(1.0, -(l + 1)));
+            for (uint64_t j = 0; j < ((uint64_t)1 << l); ++j) {
+                const double ang = (th + 2.0 * M_PI * (double)host::bitrev(j, l)) / std::ldexp(1.0, l + 1);
+                h[((size_t)1 << l) + j] = make_float2((float)(mag * std::cos(ang)), (float)(mag * std::sin(ang)));
+                hi[((size_t)1 << l) + j] = make_float2((float)(std::cos(ang) / mag), (float)(-std::sin(ang) / mag));
+            }
+        }
+        float2 *d = nullptr, *di = nullptr;
+        if (cudaMalloc(&d, n / 2 * sizeof(float2)) != cudaSuccess || cudaMalloc(&di, n / 2 * sizeof(float2)) != cudaSuccess) {
+            (void)cudaGetLastError();
+            cudaFree(d);
+            return fail(FCIRC_ENOMEM, "complex plan: cudaMalloc failed");
+        }
+        FCIRC_CUDA_TRY(cudaMemcpy(d, h.data(), n / 2 * sizeof(float2), cudaMemcpyHostToDevice));
+        FCIRC_CUDA_TRY(cudaMemcpy(di, hi.data(), n / 2 * sizeof(float2), cudaMemcpyHostToDevice));
+        it = g_cplans.emplace(key, std::make_pair(d, di)).first;
+    }
+    *tw = it->second.first;
+    *itw = it->second.second;
+    return FCIRC_OK;
+}
+
+template <class K>
+int set_smem(K kernel, int bytes)
+{
+    FCIRC_CUDA_TRY(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+    return FCIRC_OK;
+}
+
+template <int M>
+int launch_cfwd_m(const CParams &P, cudaStream_t s)
+{
+    using Sh = CShape<M>;
+    const int smem = Sh::IPC * 2 * Sh::N * (int)sizeof(float2);
+    FCIRC_TRY(set_smem(k_cfwd<M>, smem));
+    const uint64_t grid = (P.batch + Sh::IPC - 1) / Sh::IPC;
+    ProfScope ps("k_cfwd", s);
+    k_cfwd<M><<<(unsigned)grid, Sh::CT, smem, s>>>(P);
+    FCIRC_CUDA_TRY(cudaGetLastError());
+    return FCIRC_OK;
+}
+
+template <int M>
+int launch_cbwd_m(const CBwdParams &P, cudaStream_t s)
+{
+    using Sh = CShape<M>;
+    const int smem = Sh::IPC * 4 * Sh::N * (int)sizeof(float2);
+    FCIRC_TRY(set_smem(k_cbwd<M>, smem));
+    const uint64_t grid = (P.batch + Sh::IPC - 1) / Sh::IPC;
+    ProfScope ps("k_cbwd", s);
+    k_cbwd<M><<<(unsigned)grid, Sh::CT, smem, s>>>(P);
+    FCIRC_CUDA_TRY(cudaGetLastError());
+    return FCIRC_OK;
+}
+
+}  // namespace
+
+void release_cplans()
+{
+    std::lock_guard<std::mutex> lk(g_cmu);
+    for (auto &kv : g_cplans) {
+        cudaSetDevice(kv.first.dev);
+        cudaDeviceSynchronize();
+        cudaFree(kv.second.first);
+        cudaFree(kv.second.second);
+    }
+    g_cplans.clear();
+}
+
+int complex_tables(double fre, double fim, uint64_t n, const float2 **tw, const float2 **itw)
+{
+    return get_ctables(fre, fim, n, tw, itw);
+}
+
+int launch_cfwd(const CParams &P, int m, cudaStream_t s)
+{
+    switch (m) {
+    case 3: return launch_cfwd_m<3>(P, s);
+    case 4: return launch_cfwd_m<4>(P, s);
+    case 5: return launch_cfwd_m<5>(P, s);
+    case 6: return launch_cfwd_m<6>(P, s);
+    case 7: return launch_cfwd_m<7>(P, s);
+    case 8: return launch_cfwd_m<8>(P, s);
+    case 9: return launch_cfwd_m<9>(P, s);
+    case 10: return launch_cfwd_m<10>(P, s);
+    case 11: return launch_cfwd_m<11>(P, s);
+    case 12: return launch_cfwd_m<12>(P, s);
+    default: return fail(FCIRC_EINVAL, "complex product: n = 2^%d not supported", m);
+    }
+}
+
+int launch_cbwd(const CBwdParams &P, int m, cudaStream_t s)
+{
+    switch (m) {
+    case 3: return launch_cbwd_m<3>(P, s);
+    case 4: return launch_cbwd_m<4>(P, s);
+    case 5: return launch_cbwd_m<5>(P, s);
+    case 6: return launch_cbwd_m<6>(P, s);
+    case 7: return launch_cbwd_m<7>(P, s);
+    case 8: return launch_cbwd_m<8>(P, s);
+    case 9: return launch_cbwd_m<9>(P, s);
+    case 10: return launch_cbwd_m<10>(P, s);
+    case 11: return launch_cbwd_m<11>(P, s);
+    case 12: return launch_cbwd_m<12>(P, s);
+    default: return fail(FCIRC_EINVAL, "complex backward: n = 2^%d not supported", m);
+    }
+}
+
+}  // namespace fcirc

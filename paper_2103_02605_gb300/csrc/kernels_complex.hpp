@@ -1,0 +1,33 @@
+// kernels_complex.hpp -- parameter blocks of the complex FP32 kernels.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace fcirc {
+
+struct CParams {
+    const float *a, *x;
+    float *c;
+    const float2 *tw, *itw;
+    uint64_t batch;
+    float scale;   // 2^-L, the deferred halvings
+};
+
+struct CBwdParams {
+    const float *a, *x, *g;
+    float *grad_a, *grad_x;
+    const float2 *tw_x, *itw_x;   // twiddles for 1/conj(f) (dL/dx)
+    const float2 *tw_a, *itw_a;   // twiddles for conj(f) (dL/da)
+    float fc_re, fc_im;           // conj(f)
+    uint64_t batch;
+    float scale;
+};
+
+// Twiddles s_{l,j} of the product with parameter f and size n (FP64
+// rounded to FP32), cached per device.
+int complex_tables(double fre, double fim, uint64_t n, const float2 **tw, const float2 **itw);
+int launch_cfwd(const CParams &P, int m, cudaStream_t s);
+int launch_cbwd(const CBwdParams &P, int m, cudaStream_t s);
+void release_cplans();
+
+}  // namespace fcirc
