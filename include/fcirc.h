@@ -101,6 +101,63 @@ int fcirc_matvec_noalloc(uint32_t p, uint32_t f, const uint32_t *a, const uint32
                          uint32_t *c, uint64_t n, void *stream);
 
 /*
+ * fcirc_matvec_batched -- many independent products c_i = A_i x_i over
+ * Z/pZ (Algorithm 1 per instance), each with its own size and f, in one
+ * persistent launch.
+ *
+ *   p        odd prime < 2^30, common to all instances.
+ *   f        count parameters f_i (uint32).
+ *   offsets  count + 1 uint64 offsets: instance i occupies
+ *            [offsets[i], offsets[i+1]) of a, x and c; its size
+ *            n_i = offsets[i+1] - offsets[i] must be a power of two with
+ *            1 <= n_i <= 2^16 and f_i must have an (n_i/2)-th root mod p.
+ *   a, x, c  packed row vectors, vectors and results (residues).
+ *
+ * The plan of every instance (its root chain, Theorem 1) is computed on the
+ * device, so f and offsets may change between calls without any host work.
+ * The call reads offsets[count] once to size its scratch (a stream
+ * synchronisation when offsets is device memory).  An instance with a bad
+ * size or no root is skipped and reported by fcirc_sync_status
+ * (FCIRC_EINVAL / FCIRC_ENOROOT); the others are computed.
+ * Launch shape: the configuration fcirc_batched_autotune chose for the same
+ * (device, p, count, total size), else a default.
+ */
+int fcirc_matvec_batched(uint32_t p, const uint32_t *f, const uint64_t *offsets,
+                         const uint32_t *a, const uint32_t *x, uint32_t *c,
+                         uint32_t count, void *stream);
+
+/*
+ * fcirc_batched_autotune -- times every launch configuration of the batched
+ * product (persistent CTAs per SM, and the tile size -- hence the levels per
+ * in-CTA pass -- used for instances above it) on these exact arguments (device
+ * pointers), keeps the fastest for the (device, p, count, total size) of this
+ * batch, and returns its index in *chosen.  With FCIRC_TUNE_CACHE set to a
+ * file path the choices persist across processes.  Writes c.
+ */
+int fcirc_batched_autotune(uint32_t p, const uint32_t *f, const uint64_t *offsets,
+                           const uint32_t *a, const uint32_t *x, uint32_t *c,
+                           uint32_t count, void *stream, int *chosen);
+
+/* Launch configuration `index` of the batched product (for reporting). */
+int fcirc_batched_config(int index, int *ctas_per_sm, int *tile_log);
+
+/*
+ * fcirc_matvec_batched_graph -- captures the batched launch sequence for
+ * these device pointers (and the total size offsets[count] = total_n) into a
+ * CUDA graph with its own scratch; fcirc_graph_launch replays it on any
+ * stream of the same device, reading f, offsets, a, x as they are at replay
+ * time (the sizes must keep the same total).  fcirc_graph_destroy frees it.
+ * Capture this before any other capture of the calling thread.
+ */
+typedef struct fcirc_graph_s *fcirc_graph_t;
+int fcirc_matvec_batched_graph(uint32_t p, const uint32_t *f, const uint64_t *offsets,
+                               const uint32_t *a, const uint32_t *x, uint32_t *c,
+                               uint32_t count, uint64_t total_n, void *stream,
+                               fcirc_graph_t *graph);
+int fcirc_graph_launch(fcirc_graph_t graph, void *stream);
+int fcirc_graph_destroy(fcirc_graph_t graph);
+
+/*
  * poly_mul_int -- exact product of two polynomials with 16-bit unsigned
  * integer coefficients (Section 3.1): out[k] = sum_{i+j=k} P[i] Q[j] for
  * k < np + nq - 1.
@@ -177,9 +234,10 @@ int fcirc_matvec_backward(const float *a, const float *x, const float *g, double
 
 /*
  * fcirc_sync_status -- waits for `stream`, then returns and clears the
- * library's sticky device status word for the current device: FCIRC_OK, or
- * FCIRC_ETIMEOUT if a bounded device-side wait gave up since the last call,
- * or FCIRC_ECUDA if the stream reported an error.
+ * library's sticky device status word for the current device: FCIRC_OK;
+ * FCIRC_EINVAL / FCIRC_ENOROOT if an instance of a batched call had a bad
+ * size or no root; FCIRC_ETIMEOUT if a bounded device-side wait gave up;
+ * FCIRC_ECUDA if the stream reported an error.
  */
 int fcirc_sync_status(void *stream);
 

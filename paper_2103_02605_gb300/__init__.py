@@ -21,7 +21,8 @@ from . import build as _build
 __all__ = [
     "FcircError", "library_path", "load",
     "fcirc_matvec", "fcirc_matvec_noalloc", "poly_mul_int", "bigint_mul",
-    "fcirc_matvec_c64", "fcirc_matvec_backward", "fcirc_layer", "sync_status", "release",
+    "fcirc_matvec_c64", "fcirc_matvec_backward", "fcirc_layer",
+    "fcirc_matvec_batched", "batched_autotune", "BatchedGraph", "sync_status", "release",
     "nth_root", "node_twiddle", "leaf_param", "twiddle_from_factor",
     "prof_start", "prof_stop", "prof_report", "prof_launches",
     "PRIMES",
@@ -41,6 +42,12 @@ _SIGNATURES = {
     "poly_mul_int": ([_vp, _u64, _vp, _u64, _vp, _vp], _i32),
     "bigint_mul": ([_vp, _u64, _vp, _u64, _vp, _vp], _i32),
     "fcirc_matvec_c64": ([_vp, _vp, _vp, ctypes.c_double, ctypes.c_double, _u64, _u64, _vp], _i32),
+    "fcirc_matvec_batched": ([_u32, _vp, _vp, _vp, _vp, _vp, _u32, _vp], _i32),
+    "fcirc_batched_autotune": ([_u32, _vp, _vp, _vp, _vp, _vp, _u32, _vp, ctypes.POINTER(ctypes.c_int)], _i32),
+    "fcirc_batched_config": ([ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)], _i32),
+    "fcirc_matvec_batched_graph": ([_u32, _vp, _vp, _vp, _vp, _vp, _u32, _u64, _vp, ctypes.POINTER(_vp)], _i32),
+    "fcirc_graph_launch": ([_vp, _vp], _i32),
+    "fcirc_graph_destroy": ([_vp], _i32),
     "fcirc_matvec_backward": ([_vp, _vp, _vp, ctypes.c_double, ctypes.c_double, _vp, _vp, _u64, _u64, _vp],
                               _i32),
     "fcirc_sync_status": ([_vp], _i32),
@@ -183,6 +190,72 @@ def bigint_mul(A, B, out=None, stream=None):
     _check(load().bigint_mul(A.data_ptr(), A.numel(), B.data_ptr(), B.numel(), out.data_ptr(), st),
            "bigint_mul")
     return out
+
+
+def _batched_args(f, offsets, a, x, out):
+    import torch
+    for t, nm, dt in ((f, "f", (torch.int32,)), (a, "a", (torch.int32,)), (x, "x", (torch.int32,)),
+                      (offsets, "offsets", (torch.int64,))):
+        if t.dtype not in dt + tuple(getattr(torch, u) for u in ("uint32", "uint64") if hasattr(torch, u)):
+            raise TypeError(f"{nm}: unexpected dtype {t.dtype}")
+        if not t.is_contiguous() or t.dim() != 1:
+            raise ValueError(f"{nm} must be 1-D contiguous")
+    if out is None:
+        out = torch.empty_like(a)
+    return out
+
+
+def fcirc_matvec_batched(p: int, f, offsets, a, x, out=None, stream=None):
+    """Batched products c_i = A_i x_i over Z/pZ, instance i on
+    [offsets[i], offsets[i+1]) of the packed a, x, out (int32/uint32 residues;
+    offsets int64).  One persistent launch; see include/fcirc.h."""
+    out = _batched_args(f, offsets, a, x, out)
+    st = _stream_handle(stream, a, x, out)
+    _check(load().fcirc_matvec_batched(p, f.data_ptr(), offsets.data_ptr(), a.data_ptr(), x.data_ptr(),
+                                       out.data_ptr(), f.numel(), st), "fcirc_matvec_batched")
+    return out
+
+
+def batched_autotune(p: int, f, offsets, a, x, out=None, stream=None):
+    """Times every launch configuration on these arguments and keeps the
+    fastest for this batch shape; returns (index, ctas_per_sm, tile_log)."""
+    out = _batched_args(f, offsets, a, x, out)
+    st = _stream_handle(stream, a, x, out)
+    ch = ctypes.c_int(-1)
+    _check(load().fcirc_batched_autotune(p, f.data_ptr(), offsets.data_ptr(), a.data_ptr(), x.data_ptr(),
+                                         out.data_ptr(), f.numel(), st, ctypes.byref(ch)), "fcirc_batched_autotune")
+    cps, tl = ctypes.c_int(), ctypes.c_int()
+    _check(load().fcirc_batched_config(ch.value, ctypes.byref(cps), ctypes.byref(tl)), "fcirc_batched_config")
+    return ch.value, cps.value, tl.value
+
+
+class BatchedGraph:
+    """The batched launch sequence captured into a CUDA graph for fixed device
+    buffers (f, offsets, a, x, out); launch() replays it."""
+
+    def __init__(self, p: int, f, offsets, a, x, out, total_n: int, stream=None):
+        st = _stream_handle(stream, a, x, out)
+        h = _vp()
+        _check(load().fcirc_matvec_batched_graph(p, f.data_ptr(), offsets.data_ptr(), a.data_ptr(), x.data_ptr(),
+                                                 out.data_ptr(), f.numel(), total_n, st, ctypes.byref(h)),
+               "fcirc_matvec_batched_graph")
+        self._h = h
+        self._keep = (f, offsets, a, x, out)
+
+    def launch(self, stream=None):
+        st = _stream_handle(stream, *self._keep[2:])
+        _check(load().fcirc_graph_launch(self._h, st), "fcirc_graph_launch")
+
+    def destroy(self):
+        if self._h:
+            load().fcirc_graph_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
 
 
 def _c64(t, name):

@@ -5,12 +5,19 @@
 
 #include <cmath>
 
+#include <chrono>
+#include <cstdlib>
+#include <map>
+#include <mutex>
+#include <tuple>
 #include <vector>
 
 #include "common.hpp"
+#include "kernels_batched.hpp"
 #include "kernels_bigint.hpp"
 #include "kernels_complex.hpp"
 #include "kernels_mod.hpp"
+#include "prof.hpp"
 #include "ring.hpp"
 
 namespace fcirc {
@@ -503,6 +510,298 @@ int fcirc_matvec_backward(const float *a, const float *x, const float *g, double
     return st.end();
 }
 
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// batched products: configurations, autotuner cache, graph handles
+
+namespace fcirc {
+namespace {
+
+// Tunable launch shapes of the batched kernel: persistent CTAs per SM, and
+// the tile size (levels per in-CTA pass follow from it) for large instances.
+struct BConfig {
+    int ctas_per_sm;
+    int big_log;
+};
+const BConfig kBConfigs[] = {{1, 12}, {2, 12}, {3, 12}, {4, 12}, {1, 11}, {2, 11}, {3, 11}, {4, 11}};
+constexpr int kNumBConfigs = sizeof(kBConfigs) / sizeof(kBConfigs[0]);
+constexpr int kDefaultBConfig = 1;
+
+std::mutex g_tune_mu;
+std::map<std::tuple<int, uint32_t, uint32_t, uint64_t>, int> g_tune;   // (dev, p, count, total) -> config
+bool g_tune_loaded = false;
+
+const char *tune_path() { return std::getenv("FCIRC_TUNE_CACHE"); }
+
+void tune_load_locked()
+{
+    if (g_tune_loaded) return;
+    g_tune_loaded = true;
+    const char *path = tune_path();
+    if (!path) return;
+    FILE *fh = fopen(path, "r");
+    if (!fh) return;
+    int dev, cfg;
+    unsigned p, count;
+    unsigned long long total;
+    while (fscanf(fh, "%d %u %u %llu %d", &dev, &p, &count, &total, &cfg) == 5)
+        if (cfg >= 0 && cfg < kNumBConfigs) g_tune[{dev, p, count, (uint64_t)total}] = cfg;
+    fclose(fh);
+}
+
+void tune_store_locked()
+{
+    const char *path = tune_path();
+    if (!path) return;
+    FILE *fh = fopen(path, "w");
+    if (!fh) return;
+    for (auto &kv : g_tune)
+        fprintf(fh, "%d %u %u %llu %d\n", std::get<0>(kv.first), std::get<1>(kv.first), std::get<2>(kv.first),
+                (unsigned long long)std::get<3>(kv.first), kv.second);
+    fclose(fh);
+}
+
+int tuned_config(uint32_t p, uint32_t count, uint64_t total)
+{
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    tune_load_locked();
+    auto it = g_tune.find({dev, p, count, total});
+    return it == g_tune.end() ? kDefaultBConfig : it->second;
+}
+
+// Everything a batched launch needs except the per-call pointers.
+int batch_setup(uint32_t p, uint32_t count, uint64_t total, BatchParams &P)
+{
+    const PrimeTables *pt;
+    FCIRC_TRY(prime_tables(p, &pt));
+    P.p = p;
+    P.pinv = pt->pinv;
+    P.Om = pt->omega;
+    P.v = pt->v;
+    P.U = pt->d_U;
+    P.Ui = pt->d_Ui;
+    P.count = count;
+    P.total = total;
+    FCIRC_TRY(device_status_word(&P.status));
+    return FCIRC_OK;
+}
+
+int launch_with_config(BatchParams P, int cfg, cudaStream_t s)
+{
+    const BConfig &c = kBConfigs[cfg];
+    int maxc = batch_max_ctas_per_sm();
+    if (maxc <= 0) maxc = 1;
+    P.big_log = c.big_log;
+    const int cps = c.ctas_per_sm < maxc ? c.ctas_per_sm : maxc;
+    return launch_batched(P, cps, s);
+}
+
+// Total number of residues (offsets[count]) for device or host offsets.
+int batch_total(const uint64_t *offsets, uint32_t count, cudaStream_t s, uint64_t &total)
+{
+    cudaPointerAttributes attr;
+    const cudaError_t e = cudaPointerGetAttributes(&attr, offsets + count);
+    if (e != cudaSuccess) (void)cudaGetLastError();
+    if (e == cudaSuccess && (attr.type == cudaMemoryTypeDevice || attr.type == cudaMemoryTypeManaged)) {
+        FCIRC_CUDA_TRY(cudaMemcpyAsync(&total, offsets + count, 8, cudaMemcpyDeviceToHost, s));
+        FCIRC_CUDA_TRY(cudaStreamSynchronize(s));
+    } else {
+        total = offsets[count];
+    }
+    return FCIRC_OK;
+}
+
+}  // namespace
+
+struct BatchGraph {
+    int dev;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    void *scratch = nullptr;
+};
+
+}  // namespace fcirc
+
+extern "C" {
+
+int fcirc_matvec_batched(uint32_t p, const uint32_t *f, const uint64_t *offsets, const uint32_t *a,
+                         const uint32_t *x, uint32_t *c, uint32_t count, void *stream)
+{
+    set_error("");
+    if (!f || !offsets || !a || !x || !c) return fail(FCIRC_EINVAL, "fcirc_matvec_batched: null pointer");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (count == 0) return FCIRC_OK;
+    uint64_t total = 0;
+    FCIRC_TRY(batch_total(offsets, count, s, total));
+    if (total > ((uint64_t)1 << 32)) return fail(FCIRC_EINVAL, "fcirc_matvec_batched: more than 2^32 residues");
+    BatchParams P{};
+    FCIRC_TRY(batch_setup(p, count, total, P));
+    Arg af{f, (size_t)count * 4, true, false}, ao{offsets, ((size_t)count + 1) * 8, true, false};
+    Arg aa{a, total * 4, true, false}, ax{x, total * 4, true, false}, ac{c, total * 4, false, true};
+    Staging st;
+    st.args = {&af, &ao, &aa, &ax, &ac};
+    FCIRC_TRY(st.begin(s, batch_scratch_bytes(count, total)));
+    P.f = static_cast<const uint32_t *>(af.d);
+    P.offsets = static_cast<const uint64_t *>(ao.d);
+    P.a = static_cast<const uint32_t *>(aa.d);
+    P.x = static_cast<const uint32_t *>(ax.d);
+    P.c = static_cast<uint32_t *>(ac.d);
+    batch_carve(st.scratch, count, total, P);
+    FCIRC_TRY(launch_with_config(P, tuned_config(p, count, total), s));
+    return st.end();
+}
+
+int fcirc_batched_autotune(uint32_t p, const uint32_t *f, const uint64_t *offsets, const uint32_t *a,
+                           const uint32_t *x, uint32_t *c, uint32_t count, void *stream, int *chosen)
+{
+    set_error("");
+    if (!f || !offsets || !a || !x || !c) return fail(FCIRC_EINVAL, "fcirc_batched_autotune: null pointer");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (count == 0) return FCIRC_OK;
+    uint64_t total = 0;
+    FCIRC_TRY(batch_total(offsets, count, s, total));
+    BatchParams P{};
+    FCIRC_TRY(batch_setup(p, count, total, P));
+    void *scratch = nullptr;
+    FCIRC_TRY(scratch_acquire(s, batch_scratch_bytes(count, total), &scratch));
+    P.f = f;
+    P.offsets = offsets;
+    P.a = a;
+    P.x = x;
+    P.c = c;
+    batch_carve(scratch, count, total, P);
+    cudaEvent_t e0, e1;
+    FCIRC_CUDA_TRY(cudaEventCreate(&e0));
+    FCIRC_CUDA_TRY(cudaEventCreate(&e1));
+    int best = kDefaultBConfig;
+    float best_ms = 1e30f;
+    for (int cfg = 0; cfg < kNumBConfigs; ++cfg) {
+        FCIRC_TRY(launch_with_config(P, cfg, s));   // warm-up
+        float tot = 0.f;
+        for (int r = 0; r < 3; ++r) {
+            FCIRC_CUDA_TRY(cudaEventRecord(e0, s));
+            FCIRC_TRY(launch_with_config(P, cfg, s));
+            FCIRC_CUDA_TRY(cudaEventRecord(e1, s));
+            FCIRC_CUDA_TRY(cudaEventSynchronize(e1));
+            float ms = 0.f;
+            FCIRC_CUDA_TRY(cudaEventElapsedTime(&ms, e0, e1));
+            tot += ms;
+        }
+        if (tot < best_ms) {
+            best_ms = tot;
+            best = cfg;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        tune_load_locked();
+        g_tune[{dev, p, count, total}] = best;
+        tune_store_locked();
+    }
+    if (chosen) *chosen = best;
+    return FCIRC_OK;
+}
+
+int fcirc_batched_config(int index, int *ctas_per_sm, int *tile_log)
+{
+    if (index < 0 || index >= kNumBConfigs) return fail(FCIRC_EINVAL, "config index %d out of range", index);
+    if (ctas_per_sm) *ctas_per_sm = kBConfigs[index].ctas_per_sm;
+    if (tile_log) *tile_log = kBConfigs[index].big_log;
+    return FCIRC_OK;
+}
+
+int fcirc_matvec_batched_graph(uint32_t p, const uint32_t *f, const uint64_t *offsets, const uint32_t *a,
+                               const uint32_t *x, uint32_t *c, uint32_t count, uint64_t total_n, void *stream,
+                               fcirc_graph_t *out)
+{
+    set_error("");
+    if (!out || !f || !offsets || !a || !x || !c || count == 0)
+        return fail(FCIRC_EINVAL, "fcirc_matvec_batched_graph: null pointer or empty batch");
+    for (const void *ptr : {(const void *)f, (const void *)offsets, (const void *)a, (const void *)x, (const void *)c}) {
+        cudaPointerAttributes attr;
+        if (cudaPointerGetAttributes(&attr, ptr) != cudaSuccess || attr.type != cudaMemoryTypeDevice) {
+            (void)cudaGetLastError();
+            return fail(FCIRC_EINVAL, "fcirc_matvec_batched_graph: %p is not device memory", ptr);
+        }
+    }
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    BatchParams P{};
+    FCIRC_TRY(batch_setup(p, count, total_n, P));
+    BatchGraph *g = new BatchGraph();
+    FCIRC_CUDA_TRY(cudaGetDevice(&g->dev));
+    const size_t bytes = batch_scratch_bytes(count, total_n);
+    if (cudaMalloc(&g->scratch, bytes) != cudaSuccess) {
+        (void)cudaGetLastError();
+        delete g;
+        return fail(FCIRC_ENOMEM, "fcirc_matvec_batched_graph: cudaMalloc(%zu)", bytes);
+    }
+    P.f = f;
+    P.offsets = offsets;
+    P.a = a;
+    P.x = x;
+    P.c = c;
+    batch_carve(g->scratch, count, total_n, P);
+    const int cfg = tuned_config(p, count, total_n);
+    // capture on a private stream so that no other work lands in the graph
+    cudaStream_t cs;
+    FCIRC_CUDA_TRY(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    FCIRC_CUDA_TRY(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+    const int rc = launch_with_config(P, cfg, cs);
+    cudaGraph_t graph = nullptr;
+    const cudaError_t ce = cudaStreamEndCapture(cs, &graph);
+    cudaStreamDestroy(cs);
+    if (rc != FCIRC_OK || ce != cudaSuccess) {
+        (void)cudaGetLastError();
+        if (graph) cudaGraphDestroy(graph);
+        cudaFree(g->scratch);
+        delete g;
+        return rc != FCIRC_OK ? rc : fail(FCIRC_ECUDA, "graph capture failed: %s", cudaGetErrorString(ce));
+    }
+    g->graph = graph;
+    const cudaError_t ie = cudaGraphInstantiate(&g->exec, graph, 0);
+    if (ie != cudaSuccess) {
+        (void)cudaGetLastError();
+        cudaGraphDestroy(graph);
+        cudaFree(g->scratch);
+        delete g;
+        return fail(FCIRC_ECUDA, "cudaGraphInstantiate: %s", cudaGetErrorString(ie));
+    }
+    (void)s;
+    *out = reinterpret_cast<fcirc_graph_t>(g);
+    return FCIRC_OK;
+}
+
+int fcirc_graph_launch(fcirc_graph_t graph, void *stream)
+{
+    set_error("");
+    if (!graph) return fail(FCIRC_EINVAL, "fcirc_graph_launch: null graph");
+    BatchGraph *g = reinterpret_cast<BatchGraph *>(graph);
+    ProfScope ps("graph:batched", static_cast<cudaStream_t>(stream));
+    FCIRC_CUDA_TRY(cudaGraphLaunch(g->exec, static_cast<cudaStream_t>(stream)));
+    return FCIRC_OK;
+}
+
+int fcirc_graph_destroy(fcirc_graph_t graph)
+{
+    set_error("");
+    if (!graph) return FCIRC_OK;
+    BatchGraph *g = reinterpret_cast<BatchGraph *>(graph);
+    cudaSetDevice(g->dev);
+    cudaDeviceSynchronize();
+    cudaGraphExecDestroy(g->exec);
+    cudaGraphDestroy(g->graph);
+    cudaFree(g->scratch);
+    delete g;
+    return FCIRC_OK;
+}
+
 int fcirc_sync_status(void *stream)
 {
     set_error("");
@@ -514,6 +813,8 @@ int fcirc_sync_status(void *stream)
     FCIRC_CUDA_TRY(cudaMemcpy(&v, w, 4, cudaMemcpyDeviceToHost));
     if (v) {
         FCIRC_CUDA_TRY(cudaMemset(w, 0, 4));
+        if (v == FCIRC_EINVAL || v == FCIRC_ENOROOT)
+            return fail((int)v, "a batched instance was invalid or had no root (device status %u)", v);
         return fail(FCIRC_ETIMEOUT, "a bounded device-side wait gave up (code %u)", v);
     }
     return FCIRC_OK;

@@ -22,122 +22,12 @@
 #include "common.hpp"
 #include "kernels_mod.hpp"
 #include "prof.hpp"
+#include "tile_dev.cuh"
 
 namespace fcirc {
 
-// Source modes are compile-time so that every load loop is branch-free and
-// all of a thread's loads can be in flight together:
-//   bits 0-1: SrcKind; bit 2: multiply by Src::scale on load;
-//   bits 3-4: zero half of a first pass (1: below N/2, 2: from N/2).
-enum : int {
-    MODE_U32 = SRC_U32,
-    MODE_U32_S = SRC_U32 | 4,
-    MODE_REV_S = SRC_U16_REV | 4,
-    MODE_REV_S_H = SRC_U16_REV | 4 | (1 << 3),
-    MODE_U16 = SRC_U16,
-    MODE_U16_H = SRC_U16 | (2 << 3),
-};
-
-template <int MODE>
-__device__ __forceinline__ uint32_t ld_raw(const Src &s, uint32_t N, uint32_t idx)
-{
-    constexpr int KIND = MODE & 3;
-    if constexpr (KIND == SRC_U32) {
-        return static_cast<const uint32_t *>(s.ptr)[idx];
-    } else if constexpr (KIND == SRC_U16_REV) {
-        const uint32_t j = N - 1 - idx;   // a'[idx] = P[N-1-idx], P zero-padded
-        return j < s.len ? (uint32_t) static_cast<const uint16_t *>(s.ptr)[j] : 0u;
-    } else {
-        return idx < s.len ? (uint32_t) static_cast<const uint16_t *>(s.ptr)[idx] : 0u;
-    }
-}
-
-template <int MODE>
-__device__ __forceinline__ uint32_t ld_scale(uint32_t v, const Src &s, uint32_t p)
-{
-    if constexpr ((MODE & 4) != 0)
-        return shoup_mul(v, s.scale.w, s.scale.wp, p);
-    else
-        return v;
-}
-
 // ---------------------------------------------------------------------------
-// register stages.  A group of 2^NL registers v[0..2^NL) is the subtree of one
-// node: local level d pairs v[k] with v[k + h], h = 2^(NL-d-1), inside local
-// node j = k >> (NL - d); tw(d, j) is that node's twiddle (or its inverse).
-
-template <int NL, int NLEV, class TwFn>
-__device__ __forceinline__ void fwd2(uint32_t *a, uint32_t *x, TwFn tw, uint32_t p, uint32_t p2)
-{
-#pragma unroll
-    for (int d = 0; d < NLEV; ++d) {
-        const int h = (1 << NL) >> (d + 1);
-#pragma unroll
-        for (int j = 0; j < (1 << d); ++j) {
-            const Tw s = tw(d, j);
-#pragma unroll
-            for (int i = 0; i < h; ++i) {
-                const int lo = (j << (NL - d)) + i;
-                bfly_row(a[lo], a[lo + h], s, p, p2);
-                bfly_vec(x[lo], x[lo + h], s, p, p2);
-            }
-        }
-    }
-}
-
-template <int NL, bool VEC, class TwFn>
-__device__ __forceinline__ void fwd1(uint32_t *v, TwFn tw, uint32_t p, uint32_t p2)
-{
-#pragma unroll
-    for (int d = 0; d < NL; ++d) {
-        const int h = (1 << NL) >> (d + 1);
-#pragma unroll
-        for (int j = 0; j < (1 << d); ++j) {
-            const Tw s = tw(d, j);
-#pragma unroll
-            for (int i = 0; i < h; ++i) {
-                const int lo = (j << (NL - d)) + i;
-                if (VEC)
-                    bfly_vec(v[lo], v[lo + h], s, p, p2);
-                else
-                    bfly_row(v[lo], v[lo + h], s, p, p2);
-            }
-        }
-    }
-}
-
-// recombination, local levels NLEV-1 .. 0
-template <int NL, int NLEV, class TwFn>
-__device__ __forceinline__ void rec1(uint32_t *v, TwFn tw, uint32_t p, uint32_t p2)
-{
-#pragma unroll
-    for (int d = NLEV - 1; d >= 0; --d) {
-        const int h = (1 << NL) >> (d + 1);
-#pragma unroll
-        for (int j = 0; j < (1 << d); ++j) {
-            const Tw s = tw(d, j);
-#pragma unroll
-            for (int i = 0; i < h; ++i) {
-                const int lo = (j << (NL - d)) + i;
-                bfly_rec(v[lo], v[lo + h], s, p, p2);
-            }
-        }
-    }
-}
-
-// ---------------------------------------------------------------------------
-// tile kernel, 4096 residues, 256 threads
-
-// Shared-memory position of tile element e: 128-bit chunks (e >> 2) are
-// permuted inside each 128-byte row by an XOR with bits of the row index, so
-// that the three access patterns (stride 256, the 16 x 16 transpose and the
-// contiguous 16-residue groups read as 128-bit vectors) are conflict-free.
-__device__ __forceinline__ int tphi(int e)
-{
-    const int c = e >> 2, r = c >> 3, col = c & 7;
-    const int g = (r & 3) ^ ((r & 8) >> 1);
-    return (((r << 3) | (col ^ g)) << 2) | (e & 3);
-}
+// tile kernel, 4096 residues, 256 threads (the body is tile4096_dev)
 
 template <int MA, int MX>
 __global__ void __launch_bounds__(256, 3) k_tile4096(const __grid_constant__ TileParams P)
@@ -147,107 +37,8 @@ __global__ void __launch_bounds__(256, 3) k_tile4096(const __grid_constant__ Til
     __shared__ Tw STW[256];
     __shared__ Tw SITW[256];
     const TileJob &J = P.job[blockIdx.y];
-    const uint32_t p = J.p, p2 = 2 * J.p, pinv = J.pinv;
-    const int tid = threadIdx.x;
     const uint64_t t = blockIdx.x;
-    const uint64_t base = t << 12;
-    const uint32_t *sg = J.sig + t * (uint64_t)(11 * 6);   // D = 11 levels
-
-    // twiddles of tile levels 0..7 (heap index 1..255), one per thread
-    if (tid > 0) {
-        const int d = 31 - __clz(tid);
-        const uint32_t *e = sg + d * 6;
-        STW[tid] = twiddle_from(J.U[tid], e[0], e[1], e[2], p);
-        SITW[tid] = twiddle_from(J.Ui[tid], e[3], e[4], e[5], p);
-    }
-    uint32_t a[16], x[16];
-#pragma unroll
-    for (int j = 0; j < 16; ++j) {
-        a[j] = ld_raw<MA>(J.a, (uint32_t)P.N, (uint32_t)base + tid + 256 * j);
-        x[j] = ld_raw<MX>(J.x, (uint32_t)P.N, (uint32_t)base + tid + 256 * j);
-    }
-#pragma unroll
-    for (int j = 0; j < 16; ++j) {
-        a[j] = ld_scale<MA>(a[j], J.a, p);
-        x[j] = ld_scale<MX>(x[j], J.x, p);
-    }
-    __syncthreads();
-
-    // stage A: tile levels 0..3, residues tid + 256 j
-    fwd2<4, 4>(a, x, [&](int d, int j) { return STW[(1 << d) + j]; }, p, p2);
-#pragma unroll
-    for (int j = 0; j < 16; ++j) {
-        SA[tphi(tid + 256 * j)] = a[j];
-        SX[tphi(tid + 256 * j)] = x[j];
-    }
-    __syncthreads();
-    // stage B: levels 4..7, residues 256 (tid >> 4) + 16 m + (tid & 15)
-    const int eb = ((tid >> 4) << 8) + (tid & 15);
-#pragma unroll
-    for (int m = 0; m < 16; ++m) {
-        a[m] = SA[tphi(eb + 16 * m)];
-        x[m] = SX[tphi(eb + 16 * m)];
-    }
-    const int nb = tid >> 4;
-    fwd2<4, 4>(a, x, [&](int d, int j) { return STW[(1 << (4 + d)) + (nb << d) + j]; }, p, p2);
-    __syncthreads();
-#pragma unroll
-    for (int m = 0; m < 16; ++m) {
-        SA[tphi(eb + 16 * m)] = a[m];
-        SX[tphi(eb + 16 * m)] = x[m];
-    }
-    __syncthreads();
-    // stage C: levels 8..10 and the leaves, residues 16 tid .. 16 tid + 15
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-        const uint4 va = *reinterpret_cast<const uint4 *>(&SA[tphi(16 * tid + 4 * q)]);
-        const uint4 vx = *reinterpret_cast<const uint4 *>(&SX[tphi(16 * tid + 4 * q)]);
-        a[4 * q] = va.x; a[4 * q + 1] = va.y; a[4 * q + 2] = va.z; a[4 * q + 3] = va.w;
-        x[4 * q] = vx.x; x[4 * q + 1] = vx.y; x[4 * q + 2] = vx.z; x[4 * q + 3] = vx.w;
-    }
-    Tw tc[7];   // this thread's nodes: level 8 (tid), 9 (2 tid + r), 10 (4 tid + r)
-    {
-        const uint32_t *e8 = sg + 8 * 6, *e9 = sg + 9 * 6, *e10 = sg + 10 * 6;
-        tc[0] = twiddle_from(J.U[256 + tid], e8[0], e8[1], e8[2], p);
-#pragma unroll
-        for (int r = 0; r < 2; ++r) tc[1 + r] = twiddle_from(J.U[512 + 2 * tid + r], e9[0], e9[1], e9[2], p);
-#pragma unroll
-        for (int r = 0; r < 4; ++r) tc[3 + r] = twiddle_from(J.U[1024 + 4 * tid + r], e10[0], e10[1], e10[2], p);
-    }
-    fwd2<4, 3>(a, x, [&](int d, int j) { return tc[(1 << d) - 1 + j]; }, p, p2);
-#pragma unroll
-    for (int q = 0; q < 8; ++q) {
-        Tw phi = tc[3 + (q >> 1)];
-        if (q & 1) phi = tw_neg(phi, p);
-        leaf2(a[2 * q], a[2 * q + 1], x[2 * q], x[2 * q + 1], phi, p, p2, pinv);
-    }
-    {
-        const uint32_t *e8 = sg + 8 * 6, *e9 = sg + 9 * 6, *e10 = sg + 10 * 6;
-        tc[0] = twiddle_from(J.Ui[256 + tid], e8[3], e8[4], e8[5], p);
-#pragma unroll
-        for (int r = 0; r < 2; ++r) tc[1 + r] = twiddle_from(J.Ui[512 + 2 * tid + r], e9[3], e9[4], e9[5], p);
-#pragma unroll
-        for (int r = 0; r < 4; ++r) tc[3 + r] = twiddle_from(J.Ui[1024 + 4 * tid + r], e10[3], e10[4], e10[5], p);
-    }
-    rec1<4, 3>(a, [&](int d, int j) { return tc[(1 << d) - 1 + j]; }, p, p2);
-    __syncthreads();
-#pragma unroll
-    for (int q = 0; q < 4; ++q)
-        *reinterpret_cast<uint4 *>(&SA[tphi(16 * tid + 4 * q)]) =
-            make_uint4(a[4 * q], a[4 * q + 1], a[4 * q + 2], a[4 * q + 3]);
-    __syncthreads();
-#pragma unroll
-    for (int m = 0; m < 16; ++m) a[m] = SA[tphi(eb + 16 * m)];
-    rec1<4, 4>(a, [&](int d, int j) { return SITW[(1 << (4 + d)) + (nb << d) + j]; }, p, p2);
-    __syncthreads();
-#pragma unroll
-    for (int m = 0; m < 16; ++m) SA[tphi(eb + 16 * m)] = a[m];
-    __syncthreads();
-#pragma unroll
-    for (int j = 0; j < 16; ++j) a[j] = SA[tphi(tid + 256 * j)];
-    rec1<4, 4>(a, [&](int d, int j) { return SITW[(1 << d) + j]; }, p, p2);
-#pragma unroll
-    for (int j = 0; j < 16; ++j) J.dst[base + tid + 256 * j] = J.store_lazy ? a[j] : reduce_once(a[j], p);
+    tile4096_dev<MA, MX>(J, (uint32_t)P.N, (uint32_t)(t << 12), J.sig + t * (uint64_t)(11 * 6), SA, SX, STW, SITW);
 }
 
 // ---------------------------------------------------------------------------

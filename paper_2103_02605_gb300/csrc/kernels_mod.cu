@@ -24,27 +24,9 @@
 #include "common.hpp"
 #include "kernels_mod.hpp"
 #include "prof.hpp"
+#include "tile_dev.cuh"
 
 namespace fcirc {
-
-__device__ __forceinline__ uint32_t load_src(const Src &s, uint64_t N, uint64_t idx, uint32_t p)
-{
-    uint32_t v;
-    switch (s.kind) {
-    case SRC_U32:
-        v = static_cast<const uint32_t *>(s.ptr)[idx];
-        break;
-    case SRC_U16_REV: {
-        // a'[idx] = P[N-1-idx] with P zero-padded to N
-        uint64_t j = N - 1 - idx;
-        v = j < s.len ? static_cast<const uint16_t *>(s.ptr)[j] : 0u;
-        break;
-    }
-    default:  // SRC_U16
-        v = idx < s.len ? static_cast<const uint16_t *>(s.ptr)[idx] : 0u;
-    }
-    return s.scaled ? shoup_mul(v, s.scale.w, s.scale.wp, p) : v;
-}
 
 // ---------------------------------------------------------------------------
 // tile kernel
@@ -54,83 +36,9 @@ k_tile(const __grid_constant__ TileParams P)
 {
     extern __shared__ __align__(16) uint32_t smem[];
     const TileJob &J = P.job[blockIdx.y];
-    const int logT = P.logT, D = P.D;
-    const int T = 1 << logT;
-    const uint32_t p = J.p, p2 = 2 * J.p, pinv = J.pinv;
-    uint32_t *A = smem;
-    uint32_t *X = A + T;
-    Tw *tw = reinterpret_cast<Tw *>(X + T);   // [T/2], heap index 2^d + j'
-    Tw *itw = tw + (T >> 1);
     const uint64_t t = blockIdx.x;
-    const uint64_t base = t << logT;
-
-    for (int i = threadIdx.x; i < T; i += blockDim.x) {
-        A[i] = load_src(J.a, P.N, base + i, p);
-        X[i] = load_src(J.x, P.N, base + i, p);
-    }
-    if (D > 0) {
-        const uint32_t *sg = J.sig + t * (uint64_t)D * 6;
-        for (int idx = threadIdx.x + 1; idx < (1 << D); idx += blockDim.x) {
-            int d = 31 - __clz(idx);
-            const uint32_t *e = sg + d * 6;
-            tw[idx] = twiddle_from(J.U[idx], e[0], e[1], e[2], p);
-            itw[idx] = twiddle_from(J.Ui[idx], e[3], e[4], e[5], p);
-        }
-    }
-    __syncthreads();
-
-    // both input sides, levels k .. L-1 (relative 0 .. D-1)
-    for (int d = 0; d < D; ++d) {
-        const int lh = logT - d - 1;
-        const int half = 1 << lh;
-        for (int b = threadIdx.x; b < (T >> 1); b += blockDim.x) {
-            const int jn = b >> lh, i = b & (half - 1);
-            const int lo = (jn << (lh + 1)) + i, hi = lo + half;
-            const Tw s = tw[(1 << d) + jn];
-            uint32_t a0 = A[lo], a1 = A[hi];
-            bfly_row(a0, a1, s, p, p2);
-            A[lo] = a0;
-            A[hi] = a1;
-            uint32_t x0 = X[lo], x1 = X[hi];
-            bfly_vec(x0, x1, s, p, p2);
-            X[lo] = x0;
-            X[hi] = x1;
-        }
-        __syncthreads();
-    }
-    // 2x2 leaves: leaf e has parameter +s or -s of its parent node
-    for (int e = threadIdx.x; e < (T >> 1); e += blockDim.x) {
-        Tw phi;
-        if (D == 0) {
-            phi = J.rho[t];
-        } else {
-            phi = tw[(1 << (D - 1)) + (e >> 1)];
-            if (e & 1) phi = tw_neg(phi, p);
-        }
-        uint32_t a0 = A[2 * e], a1 = A[2 * e + 1];
-        leaf2(a0, a1, X[2 * e], X[2 * e + 1], phi, p, p2, pinv);
-        A[2 * e] = a0;
-        A[2 * e + 1] = a1;
-    }
-    __syncthreads();
-    // recombination, levels L-1 .. k
-    for (int d = D - 1; d >= 0; --d) {
-        const int lh = logT - d - 1;
-        const int half = 1 << lh;
-        for (int b = threadIdx.x; b < (T >> 1); b += blockDim.x) {
-            const int jn = b >> lh, i = b & (half - 1);
-            const int lo = (jn << (lh + 1)) + i, hi = lo + half;
-            uint32_t m1 = A[lo], m2 = A[hi];
-            bfly_rec(m1, m2, itw[(1 << d) + jn], p, p2);
-            A[lo] = m1;
-            A[hi] = m2;
-        }
-        __syncthreads();
-    }
-    for (int i = threadIdx.x; i < T; i += blockDim.x) {
-        uint32_t v = A[i];
-        J.dst[base + i] = J.store_lazy ? v : reduce_once(v, p);
-    }
+    const Tw rho_t = P.D == 0 ? J.rho[t] : Tw{0, 0};
+    tile_generic_dev(J, P.N, t << P.logT, P.logT, P.D, J.sig + t * (uint64_t)(P.D > 0 ? P.D : 1) * 6, rho_t, smem);
 }
 
 // ---------------------------------------------------------------------------

@@ -10,15 +10,17 @@
 #include <stdint.h>
 #include <vector>
 
+#include "modarith.cuh"   // FCIRC_HD
+
 namespace fcirc {
 namespace host {
 
-inline uint32_t mulmod(uint32_t a, uint32_t b, uint32_t p)
+FCIRC_HD uint32_t mulmod(uint32_t a, uint32_t b, uint32_t p)
 {
     return (uint32_t)((uint64_t)a * b % p);
 }
 
-inline uint32_t powmod(uint32_t b, uint64_t e, uint32_t p)
+FCIRC_HD uint32_t powmod(uint32_t b, uint64_t e, uint32_t p)
 {
     uint64_t r = 1 % p, x = b % p;
     while (e) {
@@ -29,7 +31,7 @@ inline uint32_t powmod(uint32_t b, uint64_t e, uint32_t p)
     return (uint32_t)r;
 }
 
-inline uint32_t invmod(uint32_t a, uint32_t p)  // p prime, a != 0 mod p
+FCIRC_HD uint32_t invmod(uint32_t a, uint32_t p)  // p prime, a != 0 mod p
 {
     return powmod(a, (uint64_t)p - 2, p);
 }
@@ -94,7 +96,7 @@ inline uint32_t omega(uint32_t p)
 
 // Discrete log of w in the cyclic group <Om> of order 2^v (Pohlig-Hellman,
 // one bit at a time).  Returns false if w is not in the group.
-inline bool dlog_2group(uint32_t w, uint32_t Om, int v, uint32_t p, uint64_t &out)
+FCIRC_HD bool dlog_2group(uint32_t w, uint32_t Om, int v, uint32_t p, uint64_t &out)
 {
     if (powmod(w, (uint64_t)1 << v, p) != 1) return false;
     uint32_t Om_inv = invmod(Om, p);
@@ -116,13 +118,13 @@ inline bool dlog_2group(uint32_t w, uint32_t Om, int v, uint32_t p, uint64_t &ou
 // Write p - 1 = q 2^v with q odd.  y = f^u with u = 2^-k mod q gives
 // y^(2^k) = f * z for z = (f^q)^m in the 2-Sylow subgroup <Omega>; a 2^k-th
 // root of z^-1 there is Omega^(log/2^k) when 2^k divides the discrete log.
-inline bool nth_root_2k(uint32_t f, int k, uint32_t p, uint32_t &root)
+// Same, with Omega and v supplied (usable on the device).
+FCIRC_HD bool nth_root_2k_om(uint32_t f, int k, uint32_t p, uint32_t Om, int v, uint32_t &root)
 {
     f %= p;
     if (f == 0) return false;
     if (k == 0) { root = f; return true; }
     if (f == 1) { root = 1; return true; }
-    int v = two_adic(p);
     uint64_t q = (uint64_t)(p - 1) >> v;
     // u = (2^k)^-1 mod q  (q odd; q == 1 -> u = 0)
     uint64_t u = 0;
@@ -138,7 +140,6 @@ inline bool nth_root_2k(uint32_t f, int k, uint32_t p, uint32_t &root)
     uint32_t y2k = powmod(y, (uint64_t)1 << k, p);
     uint32_t z = mulmod(y2k, invmod(f, p), p);
     uint32_t zi = invmod(z, p);
-    uint32_t Om = omega(p);
     uint64_t L;
     if (!dlog_2group(zi, Om, v, p, L)) return false;
     uint32_t w;
@@ -155,19 +156,28 @@ inline bool nth_root_2k(uint32_t f, int k, uint32_t p, uint32_t &root)
     return true;
 }
 
-inline uint32_t shoup_quot(uint32_t w, uint32_t p)  // floor(w 2^32 / p)
+inline bool nth_root_2k(uint32_t f, int k, uint32_t p, uint32_t &root)
+{
+    return nth_root_2k_om(f, k, p, omega(p), two_adic(p), root);
+}
+
+FCIRC_HD uint32_t shoup_quot(uint32_t w, uint32_t p)  // floor(w 2^32 / p)
 {
     return (uint32_t)(((uint64_t)w << 32) / p);
 }
 
-inline void shoup_quot64(uint32_t w, uint32_t p, uint32_t &hi, uint32_t &lo)
+// floor(w 2^64 / p) = (hi << 32) | lo for w < p, in two 64-bit divisions:
+// w 2^32 = hi p + r, then lo = floor(r 2^32 / p).
+FCIRC_HD void shoup_quot64(uint32_t w, uint32_t p, uint32_t &hi, uint32_t &lo)
 {
-    unsigned __int128 q = ((unsigned __int128)w << 64) / p;  // < 2^64
-    hi = (uint32_t)(q >> 32);
-    lo = (uint32_t)q;
+    const uint64_t t = (uint64_t)w << 32;
+    const uint64_t q = t / p;
+    const uint64_t r = t - q * p;
+    hi = (uint32_t)q;
+    lo = (uint32_t)((r << 32) / p);
 }
 
-inline uint32_t bitrev(uint64_t j, int bits)
+FCIRC_HD uint32_t bitrev(uint64_t j, int bits)
 {
     uint64_t r = 0;
     for (int i = 0; i < bits; ++i)
