@@ -196,19 +196,121 @@ def config_dict():
             "seed": 2103026051, "l2": "flushed (256 MiB write) between timed steps"}
 
 
-# -- roofline accounting -------------------------------------------------------------
-# Per-launch compulsory bytes of each kernel of the poly pipeline at N = 2^24:
-# every residue array is N uint32; the forward strided pass reads the two
-# uint16 inputs and writes 3 primes x 2 sides; the tile pass reads those and
-# writes 3 residue vectors; the inverse strided pass reads 3 and writes the
-# int64 coefficients.
+# -- roofline accounting ---------------------------------------------------------------
+# The kernels are bound by the SM's integer-multiply pipe (ncu:
+# sm__pipe_fmaheavy_cycles_active), not by HBM.  A 32-bit IMAD/IMUL occupies
+# that pipe for one slot per lane, a high-half or 64-bit-result multiply for
+# two; the pipe takes 16 lanes per SM sub-partition per cycle, so the peak is
+# 152 SMs x 4 x 16 slots x the SM clock.  Algorithmic slots per element, from
+# the arithmetic each kernel must do (the design doc derives them):
+#   Shoup product 4 (one high + two low), Montgomery reduction 3, 64-bit
+#   product 2, twiddle generation 8, Garner CRT 21.
+# Per circulant element N = 2^24 of the polynomial product (3 primes):
+#   k_colfwd   3 x (2 + 44) = 138   (row-vector scale, 11 levels x 2 sides)
+#   k_tile4096 3 x (44 + 22 + 9 + 8) = 249  (11 fwd levels x 2, 11 rec, leaf, twiddles)
+#   k_colinv   3 x 24 + 21 = 93     (12 rec levels, CRT)
+MUL_SLOTS_PER_ELEM = {"k_colfwd": 138, "k_tile4096": 249, "k_colinv": 93}
+SLOTS_PER_SM_CYCLE = 4 * 16
+N_SMS = 152
+
+
 def kernel_bytes():
+    """Compulsory HBM bytes of each kernel per launch (N = 2^24): every
+    residue array is N uint32."""
     N = NCIRC
     return {
-        "k_strided_fwd": 2 * NPOLY * 2 + 6 * N * 4,
-        "k_tile": 6 * N * 4 + 3 * N * 4,
-        "k_strided_inv": 3 * N * 4 + (2 * NPOLY - 1) * 8,
+        "k_colfwd": 2 * NPOLY * 2 + 6 * N * 4,
+        "k_tile4096": 6 * N * 4 + 3 * N * 4,
+        "k_colinv": 3 * N * 4 + (2 * NPOLY - 1) * 8,
     }
+
+
+def _time(fn, reps, flush, stream, warm=2):
+    import torch
+    for _ in range(warm):
+        fn()
+    torch.cuda.synchronize()
+    ts = []
+    for _ in range(reps):
+        if flush is not None:
+            flush.zero_()
+        s0 = torch.cuda.Event(enable_timing=True)
+        s1 = torch.cuda.Event(enable_timing=True)
+        s0.record(stream)
+        fn()
+        s1.record(stream)
+        torch.cuda.synchronize()
+        ts.append(s0.elapsed_time(s1))
+    return statistics.median(ts), min(ts)
+
+
+def run_extras(F, I, dev, stream):
+    """The other workloads of the method, each on its own inputs: single
+    products, the complex layer's fused forward+backward against the plain
+    three-product method, the batched launch against per-instance calls, and
+    the large-integer product.  Times in ms (median, min)."""
+    import numpy as np
+    import torch
+    out = {}
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    # single f-circulant products mod 998244353, f = 1
+    for m in (12, 24):
+        n = 1 << m
+        a, x = I.single_mod(n, seed=I.SEED_BASE + (0 if m == 12 else 10))
+        da = torch.from_numpy(a.view(np.int32)).to(dev)
+        dx = torch.from_numpy(x.view(np.int32)).to(dev)
+        dc = torch.empty_like(da)
+        med, mn = _time(lambda: F.fcirc_matvec(I.P1, 1, da, dx, out=dc, stream=stream), 20, flush, stream)
+        out[f"fcirc_matvec_n2^{m}"] = {"ms": med, "ms_min": mn, "Gelem_s": n / (med * 1e-3) / 1e9}
+    # complex layer: fused forward + backward vs forward and two plain products
+    batch, n = 4096, 1024
+    a, x, g = I.complex_layer(batch, n)
+    ta, tx, tg = (torch.from_numpy(v).to(dev) for v in (a, x, g))
+
+    def fused():
+        F.fcirc_matvec_c64(ta, tx, 1.0, stream=stream)
+        F.fcirc_matvec_backward(ta, tx, tg, 1.0, stream=stream)
+
+    def plain():
+        F.fcirc_matvec_c64(ta, tx, 1.0, stream=stream)
+        beta = torch.conj(torch.roll(torch.flip(ta, dims=[1]), 1, dims=1)).contiguous()
+        F.fcirc_matvec_c64(beta, tg, 1.0, stream=stream)                 # grad_x = A^H g
+        F.fcirc_matvec_c64(tg, torch.conj(tx).contiguous(), 1.0, stream=stream)   # grad_a
+    fm, fmin = _time(fused, 20, flush, stream)
+    pm, pmin = _time(plain, 20, flush, stream)
+    out["complex_fwd_bwd_4096x1024"] = {"fused_ms": fm, "plain_ms": pm, "speedup_vs_plain": pm / fm,
+                                        "Gelem_s": batch * n / (fm * 1e-3) / 1e9}
+    # batched: 10,000 uneven instances in one persistent graph launch vs one
+    # fcirc_matvec call per instance (plans cached by an untimed first pass)
+    nn, f, off, a, x = I.batched_mod()
+    df = torch.from_numpy(f.view(np.int32)).to(dev)
+    doff = torch.from_numpy(off.view(np.int64)).to(dev)
+    da = torch.from_numpy(a.view(np.int32)).to(dev)
+    dx = torch.from_numpy(x.view(np.int32)).to(dev)
+    dc = torch.empty_like(da)
+    tuned = F.batched_autotune(I.P1, df, doff, da, dx, out=dc, stream=stream)
+    graph = F.BatchedGraph(I.P1, df, doff, da, dx, dc, int(off[-1]), stream=stream)
+    bm, bmin = _time(lambda: graph.launch(stream=stream), 10, flush, stream)
+    views = [(da[int(off[i]):int(off[i + 1])], dx[int(off[i]):int(off[i + 1])], dc[int(off[i]):int(off[i + 1])],
+              int(f[i])) for i in range(len(nn))]
+
+    def per_instance():
+        for va, vx, vc, fi in views:
+            F.fcirc_matvec(I.P1, fi, va, vx, out=vc, stream=stream)
+    pm, _ = _time(per_instance, 1, None, stream, warm=1)
+    graph.destroy()
+    out["batched_10000_uneven"] = {"graph_ms": bm, "graph_ms_min": bmin, "per_instance_ms": pm,
+                                   "speedup_vs_per_instance": pm / bm, "Gelem_s": int(off[-1]) / (bm * 1e-3) / 1e9,
+                                   "autotuned_config": {"index": tuned[0], "ctas_per_sm": tuned[1],
+                                                        "tile_log": tuned[2]}}
+    # large integers: two 2^26-bit operands
+    A, B = I.bigint_pair()
+    tA = torch.from_numpy(A.view(np.int16)).to(dev)
+    tB = torch.from_numpy(B.view(np.int16)).to(dev)
+    to = torch.empty(A.size + B.size, dtype=torch.int16, device=dev)
+    med, mn = _time(lambda: F.bigint_mul(tA, tB, out=to, stream=stream), 10, flush, stream)
+    out["bigint_2^26bit"] = {"ms": med, "ms_min": mn, "Glimb_s": (A.size + B.size) / (med * 1e-3) / 1e9}
+    return out
 
 
 def run_ours(args, ws, rank, local):
@@ -295,19 +397,26 @@ def run_ours(args, ws, rank, local):
     dom = max(prof.items(), key=lambda kv: kv[1][1])
     dname, (dcnt, dms) = dom
     avg_s = dms / dcnt * 1e-3
-    achieved = kb.get(dname, 0) / avg_s / 1e9
+    sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    mul_peak = N_SMS * SLOTS_PER_SM_CYCLE * sm_mhz * 1e6 / 1e12          # T slots/s
+    mul_achieved = MUL_SLOTS_PER_ELEM.get(dname, 0) * NCIRC / avg_s / 1e12
+    hbm_achieved = kb.get(dname, 0) / avg_s / 1e9
     rate, m, dt, cores = oracle_rate(Pn, Qn, 10.0)
     clocks = sampler.summary(t0, t1) if sampler else {}
+    extras = run_extras(F, I, dev, stream) if (rank == 0 and not args.no_extras) else {}
     line = {
         "metric": baseline_json()["metric"],
         "value": value, "unit": "Gelem/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "u32", "data": "synthetic", "config": config_dict(),
-        "roofline": {"bound": "hbm", "kernel": dname, "achieved": achieved,
-                     "peak": float(peaks["hbm_gbs"]), "unit": "GB/s",
-                     "frac": achieved / float(peaks["hbm_gbs"]), "traffic": None,
-                     "peak_source": f"{peak_kind} hbm_gbs",
-                     "algorithmic_bytes_per_launch": kb.get(dname, 0)},
+        "roofline": {"bound": "alu", "kernel": dname, "achieved": mul_achieved,
+                     "peak": mul_peak, "unit": "T int-mul slots/s",
+                     "frac": mul_achieved / mul_peak, "traffic": None,
+                     "peak_source": f"152 SMs x 64 multiply slots/cycle x sm_max_mhz ({peak_kind} MEASURED_PEAKS clock)",
+                     "algorithmic_slots_per_launch": MUL_SLOTS_PER_ELEM.get(dname, 0) * NCIRC,
+                     "hbm": {"achieved_gbs": hbm_achieved, "peak_gbs": float(peaks["hbm_gbs"]),
+                             "frac": hbm_achieved / float(peaks["hbm_gbs"]),
+                             "compulsory_bytes_per_launch": kb.get(dname, 0)}},
         "cpu_baseline": {"value": rate / 1e9, "unit": "Gelem/s", "cores": cores, "kind": "oracle",
                          "sample": f"{m} uniformly drawn output coefficients of the same product, "
                                    f"schoolbook O(2^23) each, {dt:.1f} s"},
@@ -317,6 +426,7 @@ def run_ours(args, ws, rank, local):
         "gpu_launches": int(launches),
         "kernels": {k: {"launches": c, "avg_us": 1e3 * t / c, "share": t / sum(v[1] for v in prof.values())}
                     for k, (c, t) in sorted(prof.items())},
+        "extra": extras,
     }
     print(json.dumps(line), flush=True)
     return 0
@@ -328,6 +438,8 @@ def main():
     ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the secondary workloads reported under 'extra'")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
