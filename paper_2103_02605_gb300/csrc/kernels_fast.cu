@@ -29,8 +29,16 @@ namespace fcirc {
 // ---------------------------------------------------------------------------
 // tile kernel, 4096 residues, 256 threads (the body is tile4096_dev)
 
+// Resident CTAs per SM the kernels are compiled for (register budgets).
+#ifndef FCIRC_TILE_MINB
+#define FCIRC_TILE_MINB 3
+#endif
+#ifndef FCIRC_COLINV_MINB
+#define FCIRC_COLINV_MINB 2
+#endif
+
 template <int MA, int MX>
-__global__ void __launch_bounds__(256, 3) k_tile4096(const __grid_constant__ TileParams P)
+__global__ void __launch_bounds__(256, FCIRC_TILE_MINB) k_tile4096(const __grid_constant__ TileParams P)
 {
     __shared__ __align__(16) uint32_t SA[4096];
     __shared__ __align__(16) uint32_t SX[4096];
@@ -333,7 +341,7 @@ __device__ __forceinline__ void colinv_stage(const ColInvParams &P, uint32_t *sm
 }
 
 template <int LF, int NP>
-__global__ void __launch_bounds__(ColShape<LF>::NT) k_colinv(const __grid_constant__ ColInvParams P)
+__global__ void __launch_bounds__(ColShape<LF>::NT, NP == 1 ? FCIRC_COLINV_MINB : 1) k_colinv(const __grid_constant__ ColInvParams P)
 {
     extern __shared__ __align__(16) uint32_t sm[];
     using Sh = ColShape<LF>;
