@@ -28,15 +28,10 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-METRIC = None
+METRIC = "f-circulant matvec Gelem/s & % HBM roofline; batched/fwd+bwd speedup vs plain"
 NPOLY = 1 << 23
 NCIRC = 1 << 24
 UNITS = NCIRC  # output coefficients per step (2^24 - 1 nonzero + the padded top one)
-
-
-def baseline_json():
-    with open(os.path.join(ROOT, "BASELINE.json")) as fh:
-        return json.load(fh)
 
 
 def measured_peaks():
@@ -49,16 +44,25 @@ def measured_peaks():
 
 
 # -- distributed setup ------------------------------------------------------------
+# One process per GPU.  Every rank computes its own, independent product (its
+# own seeded inputs): the units shard across ranks with no collective on the
+# data path; the only collectives are the barrier around the timed region and
+# the max over ranks of the step time.
 
-def dist_init(n_gpus):
+def dist_init(n_gpus, backend=None):
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if ws > 1:
         import torch
         import torch.distributed as dist
-        torch.cuda.set_device(local)
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        if backend is None:
+            backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if backend == "nccl":
+            torch.cuda.set_device(local)
+            dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        else:
+            dist.init_process_group(backend)
     return ws, rank, local
 
 
@@ -73,9 +77,22 @@ def max_over_ranks(v, ws):
         return v
     import torch
     import torch.distributed as dist
-    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([v], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def rank_seed(rank):
+    """Seed of rank r's polynomial pair: rank 0 keeps the single-GPU workload."""
+    from paper_2103_02605_gb300 import inputs as I
+    return I.SEED_BASE + 1 + 1000 * rank
+
+
+def job_value(ws, ms_max):
+    """Whole-job throughput in Gelem/s: every rank's output coefficients over
+    the slowest rank's step time."""
+    return ws * UNITS / (ms_max * 1e-3) / 1e9
 
 
 # -- clocks ---------------------------------------------------------------------
@@ -175,7 +192,7 @@ def run_reference(args, ws, rank):
     tot = sum(times)
     value = per_step * len(times) / tot / 1e9
     line = {
-        "impl": "reference", "metric": baseline_json()["metric"], "value": value, "unit": "Gelem/s",
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "Gelem/s",
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * tot / len(times), "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "u64", "data": "synthetic",
@@ -193,7 +210,7 @@ def config_dict():
     return {"workload": "poly_mul_int: 2^23 x 2^23 uint16 coefficients -> 2^24 exact int64 "
                         "(f-circulant size 2^24, f = 1, primes 998244353/469762049/167772161, CRT)",
             "circulant_n": NCIRC, "poly_len": NPOLY, "primes": [998244353, 469762049, 167772161],
-            "seed": 2103026051, "l2": "flushed (256 MiB write) between timed steps"}
+            "seed": 2103026051, "seed_rank_r": "2103026051 + 1000 r", "l2": "flushed (256 MiB write) between timed steps"}
 
 
 # -- roofline accounting ---------------------------------------------------------------
@@ -202,7 +219,7 @@ def config_dict():
 # that pipe for one slot per lane, a high-half or 64-bit-result multiply for
 # two; the pipe takes 16 lanes per SM sub-partition per cycle, so the peak is
 # 152 SMs x 4 x 16 slots x the SM clock.  Algorithmic slots per element, from
-# the arithmetic each kernel must do (the design doc derives them):
+# the arithmetic each kernel must do:
 #   Shoup product 4 (one high + two low), Montgomery reduction 3, 64-bit
 #   product 2, twiddle generation 8, Garner CRT 21.
 # Per circulant element N = 2^24 of the polynomial product (3 primes):
@@ -223,6 +240,35 @@ def kernel_bytes():
         "k_tile4096": 6 * N * 4 + 3 * N * 4,
         "k_colinv": 3 * N * 4 + (2 * NPOLY - 1) * 8,
     }
+
+
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) per launch of
+# each kernel from one ncu capture of this workload, with the digest of the
+# kernel sources it was taken on; once the sources change the figure is stale
+# and the bench reports null.  profiles/poly_2e23_kernels_ncu_full.md gives
+# the command and the other counters.
+NCU_TRAFFIC = {
+    "digest": "4eb20f5f5875dd81",
+    "bytes": {"k_colfwd": 451625984, "k_tile4096": 565647104, "k_colinv": 307539456},
+}
+
+
+def kernel_source_digest():
+    import hashlib
+    d = os.path.join(ROOT, "paper_2103_02605_gb300", "csrc")
+    h = hashlib.sha256()
+    for name in sorted(os.listdir(d)):
+        if name.endswith((".cu", ".cuh", ".hpp", ".h")):
+            h.update(name.encode())
+            with open(os.path.join(d, name), "rb") as fh:
+                h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kernel):
+    if kernel_source_digest() != NCU_TRAFFIC["digest"]:
+        return None
+    return NCU_TRAFFIC["bytes"].get(kernel)
 
 
 def _time(fn, reps, flush, stream, warm=2):
@@ -323,7 +369,7 @@ def run_ours(args, ws, rank, local):
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
     F.load()
-    Pn, Qn = I.poly_pair(NPOLY)
+    Pn, Qn = I.poly_pair(NPOLY, seed=rank_seed(rank))
     P = torch.from_numpy(Pn.view(np.int16)).to(dev)
     Q = torch.from_numpy(Qn.view(np.int16)).to(dev)
     out = torch.empty(2 * NPOLY - 1, dtype=torch.int64, device=dev)
@@ -336,11 +382,11 @@ def run_ours(args, ws, rank, local):
     # correctness guard on the benchmarked call: sampled coefficients vs oracle
     step()
     torch.cuda.synchronize()
-    if rank == 0:
-        from oracle import oracle
-        idx = np.array([0, 1, NPOLY, 2 * NPOLY - 2, 777777, 12345678], dtype=np.uint64)
-        got = out[torch.from_numpy(idx.astype(np.int64)).to(dev)].cpu().numpy()
-        assert np.array_equal(got, oracle.poly_mul_coeffs(Pn, Qn, idx)), "bench output mismatch"
+    # every rank checks its own product on sampled coefficients
+    from oracle import oracle
+    idx = np.array([0, 1, NPOLY, 2 * NPOLY - 2, 777777, 12345678], dtype=np.uint64)
+    got = out[torch.from_numpy(idx.astype(np.int64)).to(dev)].cpu().numpy()
+    assert np.array_equal(got, oracle.poly_mul_coeffs(Pn, Qn, idx)), "bench output mismatch"
 
     sampler = ClockSampler(torch.cuda.current_device()) if rank == 0 else None
     if sampler:
@@ -392,7 +438,7 @@ def run_ours(args, ws, rank, local):
     if rank != 0:
         return 0
     peaks, peak_kind = measured_peaks()
-    value = ws * UNITS / (ms_max * 1e-3) / 1e9
+    value = job_value(ws, ms_max)
     kb = kernel_bytes()
     dom = max(prof.items(), key=lambda kv: kv[1][1])
     dname, (dcnt, dms) = dom
@@ -405,13 +451,13 @@ def run_ours(args, ws, rank, local):
     clocks = sampler.summary(t0, t1) if sampler else {}
     extras = run_extras(F, I, dev, stream) if (rank == 0 and not args.no_extras) else {}
     line = {
-        "metric": baseline_json()["metric"],
+        "metric": METRIC,
         "value": value, "unit": "Gelem/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "u32", "data": "synthetic", "config": config_dict(),
         "roofline": {"bound": "alu", "kernel": dname, "achieved": mul_achieved,
                      "peak": mul_peak, "unit": "T int-mul slots/s",
-                     "frac": mul_achieved / mul_peak, "traffic": None,
+                     "frac": mul_achieved / mul_peak, "traffic": ncu_traffic(dname),
                      "peak_source": f"152 SMs x 64 multiply slots/cycle x sm_max_mhz ({peak_kind} MEASURED_PEAKS clock)",
                      "algorithmic_slots_per_launch": MUL_SLOTS_PER_ELEM.get(dname, 0) * NCIRC,
                      "hbm": {"achieved_gbs": hbm_achieved, "peak_gbs": float(peaks["hbm_gbs"]),
