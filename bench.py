@@ -227,6 +227,8 @@ def config_dict():
 #   k_tile4096 3 x (44 + 22 + 9 + 8) = 249  (11 fwd levels x 2, 11 rec, leaf, twiddles)
 #   k_colinv   3 x 24 + 21 = 93     (12 rec levels, CRT)
 MUL_SLOTS_PER_ELEM = {"k_colfwd": 138, "k_tile4096": 249, "k_colinv": 93}
+MUL_SLOTS_PER_ELEM["k_colfwd4"] = MUL_SLOTS_PER_ELEM["k_colfwd"]    # same pass, four columns per thread
+MUL_SLOTS_PER_ELEM["k_colinv4"] = MUL_SLOTS_PER_ELEM["k_colinv"]
 SLOTS_PER_SM_CYCLE = 4 * 16
 N_SMS = 152
 
@@ -235,40 +237,45 @@ def kernel_bytes():
     """Compulsory HBM bytes of each kernel per launch (N = 2^24): every
     residue array is N uint32."""
     N = NCIRC
-    return {
+    b = {
         "k_colfwd": 2 * NPOLY * 2 + 6 * N * 4,
         "k_tile4096": 6 * N * 4 + 3 * N * 4,
         "k_colinv": 3 * N * 4 + (2 * NPOLY - 1) * 8,
     }
+    b["k_colfwd4"], b["k_colinv4"] = b["k_colfwd"], b["k_colinv"]
+    return b
 
 
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) per launch of
 # each kernel from one ncu capture of this workload, with the digest of the
-# kernel sources it was taken on; once the sources change the figure is stale
-# and the bench reports null.  profiles/poly_2e23_kernels_ncu_full.md gives
-# the command and the other counters.
+# source files that define the kernel when it was taken; once one of them
+# changes the figure is stale and the bench reports null.  The summaries in
+# profiles/ give the commands and the other counters.
+_KSRC = {
+    "k_colfwd4": ["kernels_col4.cu", "tile_dev.cuh", "modarith.cuh", "kernels_mod.hpp"],
+    "k_colinv": ["kernels_fast.cu", "tile_dev.cuh", "modarith.cuh", "kernels_mod.hpp"],
+    "k_tile4096": ["kernels_fast.cu", "tile_dev.cuh", "modarith.cuh", "kernels_mod.hpp"],
+}
 NCU_TRAFFIC = {
-    "digest": "4eb20f5f5875dd81",
-    "bytes": {"k_colfwd": 451625984, "k_tile4096": 565647104, "k_colinv": 307539456},
+    "k_colfwd4": (381464576, "e92066b4bdc304f1"),
 }
 
 
-def kernel_source_digest():
+def kernel_source_digest(kernel):
     import hashlib
     d = os.path.join(ROOT, "paper_2103_02605_gb300", "csrc")
     h = hashlib.sha256()
-    for name in sorted(os.listdir(d)):
-        if name.endswith((".cu", ".cuh", ".hpp", ".h")):
-            h.update(name.encode())
-            with open(os.path.join(d, name), "rb") as fh:
-                h.update(fh.read())
+    for name in _KSRC.get(kernel, sorted(os.listdir(d))):
+        h.update(name.encode())
+        with open(os.path.join(d, name), "rb") as fh:
+            h.update(fh.read())
     return h.hexdigest()[:16]
 
 
 def ncu_traffic(kernel):
-    if kernel_source_digest() != NCU_TRAFFIC["digest"]:
+    if kernel not in NCU_TRAFFIC or kernel_source_digest(kernel) != NCU_TRAFFIC[kernel][1]:
         return None
-    return NCU_TRAFFIC["bytes"].get(kernel)
+    return NCU_TRAFFIC[kernel][0]
 
 
 def _time(fn, reps, flush, stream, warm=2):

@@ -1,0 +1,694 @@
+// kernels_col4.cu -- column passes of the recursion of Algorithm 1
+// (Section 2) with four adjacent columns per thread.
+//
+// A column pass runs LF (8..12) consecutive halving levels over an array
+// viewed as 2^LF rows of 2^logS columns: level d pairs rows r and
+// r + 2^(LF-d-1) inside blocks of 2^(LF-d) rows, and every column undergoes
+// the same butterflies with the same twiddles.  A CTA of 256 threads owns
+// 2^(12-LF) column quads (16-byte row segments) over all 2^LF rows: 16384
+// residues per side and prime.  A thread holds 64 of them in registers --
+// 16 rows x 4 adjacent columns -- and runs up to four levels on them per
+// register stage; the four columns share every twiddle.  Between stages the
+// CTA exchanges residues through shared memory, 16-byte words permuted
+// within groups of 8 rows (conflict-free for every stage shape, checked
+// exhaustively on the CPU).
+//
+// Results leave through a store phase: the last stage writes shared memory,
+// and then each CTA of a two-CTA thread-block cluster (adjacent column
+// groups) writes half of the rows of both CTAs' columns, reading the peer's
+// words through distributed shared memory.  Every row segment written is
+// then 32 bytes -- whole DRAM sectors -- where the CTA alone would write
+// half sectors, which the memory system pays for as read-modify-writes.
+//
+//  * k_colfwd4<LF, M0, M1>: the forward levels of the row-vector and vector
+//    trees (one job per side and prime); blockIdx.y selects the side (0: row
+//    vector, read in source mode M0; 1: vector, mode M1).
+//  * k_colinv4<LF, NP>: the recombination levels; with NP = 3 the three
+//    primes of a polynomial product stay in shared memory and a CRT phase
+//    writes the rotated int64 coefficients.
+//
+// Inputs need 16-byte (uint32 sources) or 8-byte (uint16 sources) aligned
+// pointers; the launchers check that and otherwise leave the pass to the
+// one-column kernels of kernels_fast.cu.
+#include <atomic>
+
+#include "common.hpp"
+#include "kernels_mod.hpp"
+#include "prof.hpp"
+#include "tile_dev.cuh"
+
+namespace fcirc {
+
+namespace {
+
+constexpr int kC4Threads = 256;
+// Largest cluster, log2: two CTAs (32-byte row segments, whole DRAM sectors)
+// measured fastest; larger clusters pay more in cluster-wide waits than the
+// wider segments save.
+#ifndef FCIRC_C4_MAXLCL
+#define FCIRC_C4_MAXLCL 1
+#endif
+#ifndef FCIRC_C4FWD_MINB
+#define FCIRC_C4FWD_MINB 2
+#endif
+#ifndef FCIRC_C4INV_MINB
+#define FCIRC_C4INV_MINB 2
+#endif
+
+template <int LF>
+struct C4 {
+    static constexpr int R = 1 << LF;
+    static constexpr int LNQ = 12 - LF;            // log2 column quads per CTA
+    static constexpr int WORDS = 1 << 14;          // residues per CTA and job
+    static constexpr int NST = (LF + 3) / 4;
+    static constexpr int NL0 = LF - 4 * (NST - 1); // the first stage takes the remainder
+    static constexpr int nl(int s) { return s == 0 ? NL0 : 4; }
+    static constexpr int d0(int s) { return s == 0 ? 0 : NL0 + 4 * (s - 1); }
+    // Clusters of CL CTAs over adjacent column groups make every row segment
+    // of the coalesced store phase 2^LCQ quads (16 2^LCQ bytes) wide.
+    static constexpr int LCL0 = LNQ >= 3 ? 0 : 3 - LNQ;
+    static constexpr int LCL = LCL0 < FCIRC_C4_MAXLCL ? LCL0 : FCIRC_C4_MAXLCL;
+    static constexpr int CL = 1 << LCL;
+    static constexpr int LCQ = LNQ + LCL;            // log2 quads per row segment
+    static constexpr int LRW = LF - LCL;             // log2 rows per CTA in that phase
+};
+
+// Group slot h of thread tid in a stage running local levels D0 .. D0+NL-1:
+// its column quad, first row and level-D0 block; its rows are row0 + i 2^LST.
+template <int LF, int D0, int NL>
+__device__ __forceinline__ void c4_group(int tid, int h, int &quad, int &row0, int &blk)
+{
+    constexpr int LST = LF - D0 - NL, LRB = LF - D0, LGQ = LF - NL;
+    const int gg = tid + kC4Threads * h;
+    quad = gg >> LGQ;
+    const int g = gg & ((1 << LGQ) - 1);
+    blk = g >> LST;
+    row0 = (blk << LRB) + (g & ((1 << LST) - 1));
+}
+
+// Shared-memory word of (quad, row, column 0): 16-byte row segments, the row
+// permuted inside aligned groups of 8 by bits 4..6 of the row and by the
+// quad (its low three bits rotated), so that the 8 lanes of one 128-bit
+// access phase hit distinct banks in every stage and in the store phase.
+template <int LF>
+__device__ __forceinline__ int c4_off(int quad, int row)
+{
+    const int qs = ((quad & 3) << 1) | ((quad >> 2) & 1);
+    return (quad << (LF + 2)) + ((row ^ ((row >> 4) & 7) ^ qs) << 2);
+}
+
+// -- thread-block cluster primitives (distributed shared memory) --------------
+__device__ __forceinline__ void cl_arrive() { asm volatile("barrier.cluster.arrive.release.aligned;\n" ::: "memory"); }
+__device__ __forceinline__ void cl_wait() { asm volatile("barrier.cluster.wait.acquire.aligned;\n" ::: "memory"); }
+__device__ __forceinline__ uint32_t cl_rank()
+{
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;\n" : "=r"(r));
+    return r;
+}
+// address of the same shared-memory word in CTA `rank` of the cluster
+__device__ __forceinline__ uint32_t cl_map(uint32_t a, uint32_t rank)
+{
+    uint32_t r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;\n" : "=r"(r) : "r"(a), "r"(rank));
+    return r;
+}
+__device__ __forceinline__ uint4 cl_ld4(uint32_t a)
+{
+    uint4 v;
+    asm volatile("ld.shared::cluster.v4.u32 {%0, %1, %2, %3}, [%4];\n"
+                 : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+                 : "r"(a));
+    return v;
+}
+
+// Barrier halves over the CTAs that share row segments (the cluster, or the
+// CTA itself when CL = 1).  Every thread alternates arrive and wait.
+template <int CL>
+__device__ __forceinline__ void grp_arrive()
+{
+    if constexpr (CL > 1) cl_arrive();
+}
+template <int CL>
+__device__ __forceinline__ void grp_wait()
+{
+    if constexpr (CL > 1)
+        cl_wait();
+    else
+        __syncthreads();
+}
+
+// Shared-memory window of the CTA holding quad cq of a row segment (that CTA
+// keeps it as its quad cq & (2^LNQ - 1)); addresses are byte offsets in the
+// cluster's shared window, or in the CTA's own when CL = 1.
+template <int LF>
+__device__ __forceinline__ uint32_t c4_seg_base(const uint32_t *smq, int cq)
+{
+    using Sh = C4<LF>;
+    const uint32_t a = (uint32_t)__cvta_generic_to_shared(smq);
+    if constexpr (Sh::CL == 1)
+        return a;
+    else
+        return cl_map(a, (uint32_t)(cq >> Sh::LNQ));
+}
+
+template <int LF>
+__device__ __forceinline__ uint4 c4_seg_ld(uint32_t seg_base, int cq, int row)
+{
+    using Sh = C4<LF>;
+    const uint32_t a = seg_base + 4u * (uint32_t)c4_off<LF>(cq & ((1 << Sh::LNQ) - 1), row);
+    if constexpr (Sh::CL == 1) {
+        uint4 v;
+        asm volatile("ld.shared.v4.u32 {%0, %1, %2, %3}, [%4];\n"
+                     : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+                     : "r"(a));
+        return v;
+    } else {
+        return cl_ld4(a);
+    }
+}
+
+// Coalesced store phase: this CTA writes rows [rank 2^LRW, (rank+1) 2^LRW)
+// of all 2^LCQ quads of the cluster's columns, 2^LCQ lanes per row segment,
+// reading each 16-byte word from the CTA that computed it.  A thread
+// keeps one quad cq and steps through rows 256 / 2^LCQ apart.
+template <int LF>
+__device__ __forceinline__ void c4_store_phase(const uint32_t *smq, uint32_t *dst, uint32_t base0, int logS,
+                                               int rank, int tid)
+{
+    using Sh = C4<LF>;
+    constexpr int RSTEP = kC4Threads >> Sh::LCQ;
+    const int cq = tid & ((1 << Sh::LCQ) - 1);
+    const int row_t = (rank << Sh::LRW) + (tid >> Sh::LCQ);
+    const uint32_t sb = c4_seg_base<LF>(smq, cq);
+    uint4 *d = reinterpret_cast<uint4 *>(dst + base0 + ((uint32_t)cq << 2) + ((uint32_t)row_t << logS));
+    const size_t dstep = (size_t)RSTEP << (logS - 2);   // in uint4
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        uint4 w[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) w[k] = c4_seg_ld<LF>(sb, cq, row_t + RSTEP * (8 * h + k));
+#pragma unroll
+        for (int k = 0; k < 8; ++k) d[dstep * (8 * h + k)] = w[k];
+    }
+}
+
+// Four residues of columns idx .. idx+3 (idx a multiple of 4) in source mode MODE.
+template <int MODE>
+__device__ __forceinline__ uint4 ld4_raw(const Src &s, uint32_t N, uint32_t idx)
+{
+    constexpr int KIND = MODE & 3;
+    if constexpr (KIND == SRC_U32) {
+        return __ldg(reinterpret_cast<const uint4 *>(static_cast<const uint32_t *>(s.ptr) + idx));
+    } else if constexpr (KIND == SRC_U16_REV) {
+        // a'[idx + c] = P[N - 1 - idx - c]: P[j0 + 3 - c] with j0 = N - 4 - idx
+        const uint16_t *q = static_cast<const uint16_t *>(s.ptr);
+        const uint32_t j0 = N - 4 - idx;
+        if ((uint64_t)j0 + 4 <= s.len) {
+            const uint2 w = __ldg(reinterpret_cast<const uint2 *>(q + j0));
+            return make_uint4(w.y >> 16, w.y & 0xFFFFu, w.x >> 16, w.x & 0xFFFFu);
+        }
+        uint4 r;
+        r.x = (uint64_t)j0 + 3 < s.len ? (uint32_t)__ldg(q + j0 + 3) : 0u;
+        r.y = (uint64_t)j0 + 2 < s.len ? (uint32_t)__ldg(q + j0 + 2) : 0u;
+        r.z = (uint64_t)j0 + 1 < s.len ? (uint32_t)__ldg(q + j0 + 1) : 0u;
+        r.w = (uint64_t)j0 < s.len ? (uint32_t)__ldg(q + j0) : 0u;
+        return r;
+    } else {
+        const uint16_t *q = static_cast<const uint16_t *>(s.ptr);
+        if ((uint64_t)idx + 4 <= s.len) {
+            const uint2 w = __ldg(reinterpret_cast<const uint2 *>(q + idx));
+            return make_uint4(w.x & 0xFFFFu, w.x >> 16, w.y & 0xFFFFu, w.y >> 16);
+        }
+        uint4 r;
+        r.x = (uint64_t)idx < s.len ? (uint32_t)__ldg(q + idx) : 0u;
+        r.y = (uint64_t)idx + 1 < s.len ? (uint32_t)__ldg(q + idx + 1) : 0u;
+        r.z = (uint64_t)idx + 2 < s.len ? (uint32_t)__ldg(q + idx + 2) : 0u;
+        r.w = (uint64_t)idx + 3 < s.len ? (uint32_t)__ldg(q + idx + 3) : 0u;
+        return r;
+    }
+}
+
+// Twiddles of local level D of one group (slots 16 - 2^(D+1) .. 16 - 2^D of
+// its 16-entry block in the group-ordered table), in 64/128-bit loads.
+template <int D>
+__device__ __forceinline__ void c4_level_tw(const Tw *g, Tw *t)
+{
+    if constexpr (D == 0) {
+        const uint2 w = __ldg(reinterpret_cast<const uint2 *>(g + 14));
+        t[0] = Tw{w.x, w.y};
+    } else {
+        const uint4 *q = reinterpret_cast<const uint4 *>(g + 16 - (2 << D));
+#pragma unroll
+        for (int k = 0; k < (1 << (D - 1)); ++k) {
+            const uint4 w = __ldg(q + k);
+            t[2 * k] = Tw{w.x, w.y};
+            t[2 * k + 1] = Tw{w.z, w.w};
+        }
+    }
+}
+
+// Forward levels D .. NL-1 of one group held as v[4 i + c] (row i, column
+// c); `cur` holds level D's twiddles, level D+1's are loaded before level D
+// is computed.
+template <int NL, int D, bool VEC>
+__device__ __forceinline__ void c4_fwd(uint32_t *v, const Tw *g, const Tw *cur, uint32_t p, uint32_t p2)
+{
+    if constexpr (D < NL) {
+        Tw nxt[(D + 1 < NL) ? (2 << D) : 1];
+        if constexpr (D + 1 < NL) c4_level_tw<D + 1>(g, nxt);
+        constexpr int h = (1 << NL) >> (D + 1);
+#pragma unroll
+        for (int j = 0; j < (1 << D); ++j)
+#pragma unroll
+            for (int i = 0; i < h; ++i) {
+                const int lo = (j << (NL - D)) + i;
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    if (VEC)
+                        bfly_vec(v[4 * lo + c], v[4 * (lo + h) + c], cur[j], p, p2);
+                    else
+                        bfly_row(v[4 * lo + c], v[4 * (lo + h) + c], cur[j], p, p2);
+                }
+            }
+        c4_fwd<NL, D + 1, VEC>(v, g, nxt, p, p2);
+    }
+}
+
+// Recombination levels D .. 0 of one group (inverse twiddles), with the
+// same one-level look-ahead of twiddle loads.
+template <int NL, int D>
+__device__ __forceinline__ void c4_rec(uint32_t *v, const Tw *g, const Tw *cur, uint32_t p, uint32_t p2)
+{
+    if constexpr (D >= 0) {
+        Tw nxt[D > 0 ? (1 << (D - 1)) : 1];
+        if constexpr (D > 0) c4_level_tw<D - 1>(g, nxt);
+        constexpr int h = (1 << NL) >> (D + 1);
+#pragma unroll
+        for (int j = 0; j < (1 << D); ++j)
+#pragma unroll
+            for (int i = 0; i < h; ++i) {
+                const int lo = (j << (NL - D)) + i;
+#pragma unroll
+                for (int c = 0; c < 4; ++c) bfly_rec(v[4 * lo + c], v[4 * (lo + h) + c], cur[j], p, p2);
+            }
+        c4_rec<NL, D - 1>(v, g, nxt, p, p2);
+    }
+}
+
+__device__ __forceinline__ void put4(uint32_t *v, uint4 w)
+{
+    v[0] = w.x;
+    v[1] = w.y;
+    v[2] = w.z;
+    v[3] = w.w;
+}
+
+__device__ __forceinline__ uint4 get4(const uint32_t *v) { return make_uint4(v[0], v[1], v[2], v[3]); }
+
+template <int LF, int S, int MODE, bool VEC>
+__device__ __forceinline__ void c4fwd_stage(const ColFwdJob &J, const ColFwdParams &P, uint32_t *sm,
+                                            uint32_t base, uint32_t pb, int logS, int tid, bool wait_first)
+{
+    using Sh = C4<LF>;
+    constexpr int NL = Sh::nl(S), D0 = Sh::d0(S);
+    constexpr int M = 1 << NL, B = 16 >> NL, LST = LF - D0 - NL;
+    constexpr bool FIRST = (S == 0);
+    constexpr int half = FIRST ? ((MODE >> 3) & 3) : 0;
+    const uint32_t p = J.p, p2 = 2 * J.p;
+    const Tw *gt = J.gtw + P.stage_off[S];
+    uint32_t v[64];
+    // every load of the stage is issued before any arithmetic
+#pragma unroll
+    for (int hb = 0; hb < B; ++hb) {
+        int quad, row0, blk;
+        c4_group<LF, D0, NL>(tid, hb, quad, row0, blk);
+#pragma unroll
+        for (int i = 0; i < M; ++i) {
+            if ((half == 1 && i < M / 2) || (half == 2 && i >= M / 2)) continue;
+            const int row = row0 + (i << LST);
+            uint4 w;
+            if constexpr (FIRST)
+                w = ld4_raw<MODE>(J.src, P.N, base + ((uint32_t)quad << 2) + ((uint32_t)row << logS));
+            else
+                w = *reinterpret_cast<const uint4 *>(sm + c4_off<LF>(quad, row));
+            put4(v + 4 * (hb * M + i), w);
+        }
+    }
+#pragma unroll
+    for (int hb = 0; hb < B; ++hb) {
+        int quad, row0, blk;
+        c4_group<LF, D0, NL>(tid, hb, quad, row0, blk);
+        const Tw *g = gt + (((pb << D0) + blk) << 4);
+        constexpr int DS = (FIRST && half != 0) ? 1 : 0;
+        Tw t0[1 << DS];
+        c4_level_tw<DS>(g, t0);
+        uint32_t *vg = v + 4 * hb * M;
+        if constexpr (FIRST) {
+#pragma unroll
+            for (int i = 0; i < M; ++i) {
+                if ((half == 1 && i < M / 2) || (half == 2 && i >= M / 2)) continue;
+#pragma unroll
+                for (int c = 0; c < 4; ++c) vg[4 * i + c] = ld_scale<MODE>(vg[4 * i + c], J.src, p);
+            }
+            if constexpr (half == 1) {
+                // row vector zero in rows < R/2; level 0 has s = 1: (0 + hi, 0 - hi)
+#pragma unroll
+                for (int i = M / 2; i < M; ++i)
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) {
+                        const uint32_t x = vg[4 * i + c];
+                        vg[4 * (i - M / 2) + c] = x;
+                        vg[4 * i + c] = p2 - x;
+                    }
+            } else if constexpr (half == 2) {
+                // vector zero in rows >= R/2; level 0 has s = 1: (lo, lo)
+#pragma unroll
+                for (int i = 0; i < M / 2; ++i)
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) vg[4 * (i + M / 2) + c] = vg[4 * i + c];
+            }
+        }
+        c4_fwd<NL, DS, VEC>(vg, g, t0, p, p2);
+    }
+    // the previous job's store phase may still read this CTA's shared memory
+    if (FIRST && wait_first) grp_wait<Sh::CL>();
+#pragma unroll
+    for (int hb = 0; hb < B; ++hb) {
+        int quad, row0, blk;
+        c4_group<LF, D0, NL>(tid, hb, quad, row0, blk);
+#pragma unroll
+        for (int i = 0; i < M; ++i) {
+            const int row = row0 + (i << LST);
+            *reinterpret_cast<uint4 *>(sm + c4_off<LF>(quad, row)) = get4(v + 4 * (hb * M + i));
+        }
+    }
+}
+
+template <int LF, int MODE, bool VEC>
+__device__ __forceinline__ void c4fwd_jobs(const ColFwdParams &P, uint32_t *sm, int j0, uint32_t base,
+                                           uint32_t pb, int logS, int tid)
+{
+    using Sh = C4<LF>;
+    const int rank = Sh::CL > 1 ? (int)cl_rank() : 0;
+    const uint32_t base0 = base - ((uint32_t)rank << (2 + Sh::LNQ));
+#pragma unroll 1
+    for (int jj = 0; jj < P.jobs_per_cta; ++jj) {
+        const ColFwdJob &J = P.job[j0 + jj];
+        c4fwd_stage<LF, 0, MODE, VEC>(J, P, sm, base, pb, logS, tid, jj > 0);
+        if constexpr (Sh::NST > 1) {
+            __syncthreads();
+            c4fwd_stage<LF, 1, MODE, VEC>(J, P, sm, base, pb, logS, tid, false);
+        }
+        if constexpr (Sh::NST > 2) {
+            __syncthreads();
+            c4fwd_stage<LF, 2, MODE, VEC>(J, P, sm, base, pb, logS, tid, false);
+        }
+        grp_arrive<Sh::CL>();
+        grp_wait<Sh::CL>();
+        c4_store_phase<LF>(sm, J.dst, base0, logS, rank, tid);
+        grp_arrive<Sh::CL>();
+    }
+    grp_wait<Sh::CL>();   // no CTA leaves while a peer still reads its shared memory
+}
+
+// CTA origin: node pb of level l0 and the CTA's first column
+template <int LF>
+__device__ __forceinline__ void c4_origin(int logn, int l0, int l1, uint32_t &pb, uint32_t &base, int &logS)
+{
+    logS = logn - l1;
+    const int cg_bits = logS - 2 - C4<LF>::LNQ;
+    pb = blockIdx.x >> cg_bits;
+    const uint32_t cg = blockIdx.x & ((1u << cg_bits) - 1);
+    base = (pb << (logn - l0)) + (cg << (2 + C4<LF>::LNQ));
+}
+
+template <int LF, int M0, int M1>
+__global__ void __cluster_dims__(C4<LF>::CL, 1, 1) __launch_bounds__(kC4Threads, FCIRC_C4FWD_MINB) k_colfwd4(const __grid_constant__ ColFwdParams P)
+{
+    extern __shared__ __align__(16) uint32_t sm[];
+    uint32_t pb, base;
+    int logS;
+    c4_origin<LF>(P.logn, P.l0, P.l1, pb, base, logS);
+    const int j0 = blockIdx.y * P.jobs_per_cta;
+    // job group 0 is the row-vector side, group 1 the vector side
+    if (blockIdx.y == 0)
+        c4fwd_jobs<LF, M0, false>(P, sm, j0, base, pb, logS, threadIdx.x);
+    else
+        c4fwd_jobs<LF, M1, true>(P, sm, j0, base, pb, logS, threadIdx.x);
+}
+
+template <int LF, int NP, int S>
+__device__ __forceinline__ void c4inv_stage(const ColInvParams &P, uint32_t *sm, uint32_t base, uint32_t pb,
+                                            int logS, int tid)
+{
+    using Sh = C4<LF>;
+    constexpr int NL = Sh::nl(S), D0 = Sh::d0(S);
+    constexpr int M = 1 << NL, B = 16 >> NL, LST = LF - D0 - NL;
+    constexpr bool FIRST = (S == Sh::NST - 1), LAST = (S == 0);
+#pragma unroll 1
+    for (int q = 0; q < NP; ++q) {
+        const ColInvJob &J = P.job[q];
+        const uint32_t p = J.p, p2 = 2 * J.p;
+        uint32_t *smq = sm + q * Sh::WORDS;
+        const Tw *gt = J.gitw + P.stage_off[S];
+        uint32_t v[64];
+#pragma unroll
+        for (int hb = 0; hb < B; ++hb) {
+            int quad, row0, blk;
+            c4_group<LF, D0, NL>(tid, hb, quad, row0, blk);
+#pragma unroll
+            for (int i = 0; i < M; ++i) {
+                const int row = row0 + (i << LST);
+                uint4 w;
+                if constexpr (FIRST)
+                    w = __ldg(reinterpret_cast<const uint4 *>(J.src + base + ((uint32_t)quad << 2) +
+                                                              ((uint32_t)row << logS)));
+                else
+                    w = *reinterpret_cast<const uint4 *>(smq + c4_off<LF>(quad, row));
+                put4(v + 4 * (hb * M + i), w);
+            }
+        }
+#pragma unroll
+        for (int hb = 0; hb < B; ++hb) {
+            int quad, row0, blk;
+            c4_group<LF, D0, NL>(tid, hb, quad, row0, blk);
+            const Tw *g = gt + (((pb << D0) + blk) << 4);
+            Tw tl[1 << (NL - 1)];
+            c4_level_tw<NL - 1>(g, tl);
+            c4_rec<NL, NL - 1>(v + 4 * hb * M, g, tl, p, p2);
+        }
+        // the last stage leaves canonical residues unless the output stays lazy
+        const bool canon = LAST && P.epi != EPI_LAZY;
+#pragma unroll
+        for (int hb = 0; hb < B; ++hb) {
+            int quad, row0, blk;
+            c4_group<LF, D0, NL>(tid, hb, quad, row0, blk);
+#pragma unroll
+            for (int i = 0; i < M; ++i) {
+                const int row = row0 + (i << LST);
+                uint32_t *e = v + 4 * (hb * M + i);
+                const uint4 w = canon ? make_uint4(reduce_once(e[0], p), reduce_once(e[1], p),
+                                                   reduce_once(e[2], p), reduce_once(e[3], p))
+                                      : get4(e);
+                *reinterpret_cast<uint4 *>(smq + c4_off<LF>(quad, row)) = w;
+            }
+        }
+    }
+}
+
+// CRT phase of the polynomial product: the rows of the store phase, the three
+// primes' canonical residues from the CTA that computed them, Garner's CRT,
+// and the int64 coefficient stored rotated by one (c_k = d_{k+1}).
+template <int LF>
+__device__ __forceinline__ void c4_crt_phase(const ColInvParams &P, const uint32_t *sm, uint32_t base0, int logS,
+                                             int rank, int tid)
+{
+    using Sh = C4<LF>;
+    constexpr int RSTEP = kC4Threads >> Sh::LCQ;
+    const uint32_t mask = P.N - 1;
+    const int cq = tid & ((1 << Sh::LCQ) - 1);
+    const int row_t = (rank << Sh::LRW) + (tid >> Sh::LCQ);
+    const uint32_t sb = c4_seg_base<LF>(sm, cq);
+    constexpr uint32_t PB = 4u * Sh::WORDS;   // bytes per prime region
+#pragma unroll 2
+    for (int k = 0; k < 16; ++k) {
+        const int row = row_t + RSTEP * k;
+        const uint4 r1 = c4_seg_ld<LF>(sb, cq, row);
+        const uint4 r2 = c4_seg_ld<LF>(sb + PB, cq, row);
+        const uint4 r3 = c4_seg_ld<LF>(sb + 2 * PB, cq, row);
+        const uint32_t idx = base0 + ((uint32_t)cq << 2) + ((uint32_t)row << logS);
+        const uint32_t d0 = (idx + mask) & mask;   // c_k = d_{k+1}
+        if (d0 < P.nout) P.dst64[d0] = crt3(r1.x, r2.x, r3.x, P.crt);
+        if (idx < P.nout) P.dst64[idx] = crt3(r1.y, r2.y, r3.y, P.crt);
+        if (idx + 1 < P.nout) P.dst64[idx + 1] = crt3(r1.z, r2.z, r3.z, P.crt);
+        if (idx + 2 < P.nout) P.dst64[idx + 2] = crt3(r1.w, r2.w, r3.w, P.crt);
+    }
+}
+
+template <int LF, int NP>
+__global__ void __cluster_dims__(C4<LF>::CL, 1, 1) __launch_bounds__(kC4Threads, NP == 1 ? FCIRC_C4INV_MINB : 1)
+    k_colinv4(const __grid_constant__ ColInvParams P)
+{
+    extern __shared__ __align__(16) uint32_t sm[];
+    using Sh = C4<LF>;
+    uint32_t pb, base;
+    int logS;
+    c4_origin<LF>(P.logn, P.l0, P.l1, pb, base, logS);
+    const int tid = threadIdx.x;
+    const int rank = Sh::CL > 1 ? (int)cl_rank() : 0;
+    const uint32_t base0 = base - ((uint32_t)rank << (2 + Sh::LNQ));
+    if constexpr (Sh::NST > 2) {
+        c4inv_stage<LF, NP, 2>(P, sm, base, pb, logS, tid);
+        __syncthreads();
+    }
+    if constexpr (Sh::NST > 1) {
+        c4inv_stage<LF, NP, 1>(P, sm, base, pb, logS, tid);
+        __syncthreads();
+    }
+    c4inv_stage<LF, NP, 0>(P, sm, base, pb, logS, tid);
+    grp_arrive<Sh::CL>();
+    grp_wait<Sh::CL>();
+    if (NP == 3 && P.epi == EPI_CRT_ROT) {
+        c4_crt_phase<LF>(P, sm, base0, logS, rank, tid);
+    } else {
+#pragma unroll 1
+        for (int q = 0; q < NP; ++q) c4_store_phase<LF>(sm + q * Sh::WORDS, P.job[q].dst, base0, logS, rank, tid);
+    }
+    // no CTA leaves while a peer still reads its shared memory
+    grp_arrive<Sh::CL>();
+    grp_wait<Sh::CL>();
+}
+
+template <class K>
+int c4_smem(K kernel, int bytes, std::atomic<unsigned> &mask)
+{
+    int dev = 0;
+    FCIRC_CUDA_TRY(cudaGetDevice(&dev));
+    const unsigned bit = 1u << (dev & 31);
+    if (mask.load() & bit) return FCIRC_OK;
+    FCIRC_CUDA_TRY(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+    mask.fetch_or(bit);
+    return FCIRC_OK;
+}
+
+int c4_mode(const Src &s, int half) { return s.kind | (s.scaled ? 4 : 0) | (half << 3); }
+
+bool aligned(const void *ptr, unsigned a) { return (reinterpret_cast<uintptr_t>(ptr) & (a - 1)) == 0; }
+
+bool src_aligned(const Src &s)
+{
+    return s.kind == SRC_U32 ? aligned(s.ptr, 16) : aligned(s.ptr, 8);
+}
+
+template <int LF, int M0, int M1>
+int launch_c4fwd_m(const ColFwdParams &P, int nctay, cudaStream_t s)
+{
+    static std::atomic<unsigned> mask{0};
+    const int smem = C4<LF>::WORDS * 4;
+    FCIRC_TRY(c4_smem(k_colfwd4<LF, M0, M1>, smem, mask));
+    const uint64_t ncta = (uint64_t)1 << (P.l0 + (P.logn - P.l1) - 2 - C4<LF>::LNQ);
+    dim3 grid((unsigned)ncta, nctay);
+    ProfScope ps("k_colfwd4", s);
+    k_colfwd4<LF, M0, M1><<<grid, kC4Threads, smem, s>>>(P);
+    FCIRC_CUDA_TRY(cudaGetLastError());
+    return FCIRC_OK;
+}
+
+template <int LF>
+int launch_c4fwd_lf(const ColFwdParams &P, int nctay, int m0, int m1, cudaStream_t s)
+{
+    if (m0 == MODE_U32_S && m1 == MODE_U32) return launch_c4fwd_m<LF, MODE_U32_S, MODE_U32>(P, nctay, s);
+    if (m0 == MODE_U32 && m1 == MODE_U32) return launch_c4fwd_m<LF, MODE_U32, MODE_U32>(P, nctay, s);
+    if (m0 == MODE_REV_S_H && m1 == MODE_U16_H) return launch_c4fwd_m<LF, MODE_REV_S_H, MODE_U16_H>(P, nctay, s);
+    if (m0 == MODE_REV_S && m1 == MODE_U16) return launch_c4fwd_m<LF, MODE_REV_S, MODE_U16>(P, nctay, s);
+    return fail(FCIRC_EINVAL, "column pass: unsupported source modes %d/%d", m0, m1);
+}
+
+template <int LF, int NP>
+int launch_c4inv_lf(const ColInvParams &P, cudaStream_t s)
+{
+    static std::atomic<unsigned> mask{0};
+    const int smem = NP * C4<LF>::WORDS * 4;
+    FCIRC_TRY(c4_smem(k_colinv4<LF, NP>, smem, mask));
+    const uint64_t ncta = (uint64_t)1 << (P.l0 + (P.logn - P.l1) - 2 - C4<LF>::LNQ);
+    ProfScope ps("k_colinv4", s);
+    k_colinv4<LF, NP><<<(unsigned)ncta, kC4Threads, smem, s>>>(P);
+    FCIRC_CUDA_TRY(cudaGetLastError());
+    return FCIRC_OK;
+}
+
+}  // namespace
+
+// The pass can run here: LF in 8..12, enough columns for one cluster's
+// quads, and 16-byte (uint32) / 8-byte (uint16) aligned sources and
+// destinations.
+bool col4_fwd_ok(const ColFwdParams &P, int nctay)
+{
+    const int lf = P.l1 - P.l0, logS = P.logn - P.l1;
+    // every cluster's column groups lie in one level-l0 block
+    if (lf < 8 || lf > 12 || logS < 2 + ((12 - lf) > 3 ? 12 - lf : 3)) return false;
+    if (nctay > 2) return false;
+    for (int k = 0; k < nctay * P.jobs_per_cta; ++k)
+        if (!src_aligned(P.job[k].src) || !aligned(P.job[k].dst, 16) ||
+            P.job[k].vec_side != k / P.jobs_per_cta)
+            return false;
+    return true;
+}
+
+bool col4_inv_ok(const ColInvParams &P)
+{
+    const int lf = P.l1 - P.l0, logS = P.logn - P.l1;
+    // every cluster's column groups lie in one level-l0 block
+    if (lf < 8 || lf > 12 || logS < 2 + ((12 - lf) > 3 ? 12 - lf : 3)) return false;
+    // three primes: the one-column kernel (16 warps per SM) is faster
+    if (P.nprime != 1) return false;
+    for (int q = 0; q < P.nprime; ++q)
+        if (!aligned(P.job[q].src, 16) || (P.epi != EPI_CRT_ROT && !aligned(P.job[q].dst, 16))) return false;
+    return true;
+}
+
+int launch_colfwd4(const ColFwdParams &P, int nctay, cudaStream_t s)
+{
+    const int m0 = c4_mode(P.job[0].src, P.job[0].half);
+    const int m1 = nctay > 1 ? c4_mode(P.job[P.jobs_per_cta].src, P.job[P.jobs_per_cta].half) : MODE_U32;
+    for (int g = 0; g < nctay; ++g)
+        for (int k = 0; k < P.jobs_per_cta; ++k) {
+            const ColFwdJob &J = P.job[g * P.jobs_per_cta + k];
+            if (c4_mode(J.src, J.half) != (g == 0 ? m0 : m1))
+                return fail(FCIRC_EINVAL, "column pass: mixed source modes in one job group");
+        }
+    switch (P.l1 - P.l0) {
+    case 8: return launch_c4fwd_lf<8>(P, nctay, m0, m1, s);
+    case 9: return launch_c4fwd_lf<9>(P, nctay, m0, m1, s);
+    case 10: return launch_c4fwd_lf<10>(P, nctay, m0, m1, s);
+    case 11: return launch_c4fwd_lf<11>(P, nctay, m0, m1, s);
+    case 12: return launch_c4fwd_lf<12>(P, nctay, m0, m1, s);
+    default: return fail(FCIRC_EINVAL, "column pass of %d levels", P.l1 - P.l0);
+    }
+}
+
+int launch_colinv4(const ColInvParams &P, cudaStream_t s)
+{
+    const int lf = P.l1 - P.l0;
+    if (P.nprime == 1) {
+        switch (lf) {
+        case 8: return launch_c4inv_lf<8, 1>(P, s);
+        case 9: return launch_c4inv_lf<9, 1>(P, s);
+        case 10: return launch_c4inv_lf<10, 1>(P, s);
+        case 11: return launch_c4inv_lf<11, 1>(P, s);
+        case 12: return launch_c4inv_lf<12, 1>(P, s);
+        }
+    } else if (P.nprime == 3) {
+        switch (lf) {
+        case 8: return launch_c4inv_lf<8, 3>(P, s);
+        case 9: return launch_c4inv_lf<9, 3>(P, s);
+        case 10: return launch_c4inv_lf<10, 3>(P, s);
+        case 11: return launch_c4inv_lf<11, 3>(P, s);
+        case 12: return launch_c4inv_lf<12, 3>(P, s);
+        }
+    }
+    return fail(FCIRC_EINVAL, "column pass of %d levels, %d primes", lf, P.nprime);
+}
+
+}  // namespace fcirc

@@ -33,6 +33,12 @@ namespace fcirc {
 #ifndef FCIRC_TILE_MINB
 #define FCIRC_TILE_MINB 3
 #endif
+#ifndef FCIRC_COL4
+#define FCIRC_COL4 1
+#endif
+#ifndef FCIRC_COLFWD_MINB
+#define FCIRC_COLFWD_MINB 2
+#endif
 #ifndef FCIRC_COLINV_MINB
 #define FCIRC_COLINV_MINB 2
 #endif
@@ -252,7 +258,7 @@ __device__ __forceinline__ void colfwd_jobs(const ColFwdParams &P, uint32_t *sm,
 // blockIdx.y selects a group of jobs_per_cta jobs; group 0 reads its input
 // in mode M0, group 1 in mode M1
 template <int LF, int M0, int M1>
-__global__ void __launch_bounds__(ColShape<LF>::NT, 2) k_colfwd(const __grid_constant__ ColFwdParams P)
+__global__ void __launch_bounds__(ColShape<LF>::NT, FCIRC_COLFWD_MINB) k_colfwd(const __grid_constant__ ColFwdParams P)
 {
     extern __shared__ __align__(16) uint32_t sm[];
     using Sh = ColShape<LF>;
@@ -436,6 +442,9 @@ static int launch_colfwd_lf(const ColFwdParams &P, int nctay, cudaStream_t s)
 
 int launch_colfwd(const ColFwdParams &P, int nctay, cudaStream_t s)
 {
+#if FCIRC_COL4
+    if (col4_fwd_ok(P, nctay)) return launch_colfwd4(P, nctay, s);
+#endif
     switch (P.l1 - P.l0) {
     case 8: return launch_colfwd_lf<8>(P, nctay, s);
     case 9: return launch_colfwd_lf<9>(P, nctay, s);
@@ -461,6 +470,9 @@ static int launch_colinv_lf(const ColInvParams &P, cudaStream_t s)
 
 int launch_colinv(const ColInvParams &P, cudaStream_t s)
 {
+#if FCIRC_COL4
+    if (col4_inv_ok(P)) return launch_colinv4(P, s);
+#endif
     const int lf = P.l1 - P.l0;
     if (P.nprime == 1) {
         switch (lf) {

@@ -154,6 +154,11 @@ bool fast_col_ok(int lf, int logS);
 int launch_tile_fast(const TileParams &P, uint64_t ntiles, int njobs, cudaStream_t s);
 int launch_colfwd(const ColFwdParams &P, int nctay, cudaStream_t s);
 int launch_colinv(const ColInvParams &P, cudaStream_t s);
+// four columns per thread (kernels_col4.cu); used when these accept the pass
+bool col4_fwd_ok(const ColFwdParams &P, int nctay);
+bool col4_inv_ok(const ColInvParams &P);
+int launch_colfwd4(const ColFwdParams &P, int nctay, cudaStream_t s);
+int launch_colinv4(const ColInvParams &P, cudaStream_t s);
 // stage split of a column pass of lf levels: the first stage takes lf mod 4
 // (or 4), the others 4 levels each
 inline int col_nstage(int lf) { return (lf + 3) / 4; }

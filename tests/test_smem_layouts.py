@@ -1,0 +1,131 @@
+"""Shared-memory layouts of the register-staged kernels, checked exhaustively
+on the CPU: every access pattern is a bijection onto the buffer (no two
+threads' residues collide) and every warp access is free of bank conflicts.
+
+The index formulas are restated from csrc/tile_dev.cuh (tphi, the 4096-residue
+tile), csrc/kernels_fast.cu (cphi, one column per thread) and
+csrc/kernels_col4.cu (c4_off and the store phase, four columns per thread).
+Banks: 32 four-byte banks; a 128-bit access is served in four phases of
+eight lanes, each of which must touch eight distinct 16-byte bank groups."""
+from collections import Counter
+
+import pytest
+
+
+# -- 4096-residue tile -----------------------------------------------------------
+
+def tphi(e):
+    c = e >> 2
+    r, col = c >> 3, c & 7
+    g = (r & 3) ^ ((r & 8) >> 1)
+    return (((r << 3) | (col ^ g)) << 2) | (e & 3)
+
+
+def test_tile_layout_bijective():
+    assert sorted(tphi(e) for e in range(4096)) == list(range(4096))
+
+
+def test_tile_scalar_patterns_conflict_free():
+    # stage A: residues tid + 256 j; stage B: 256 (tid >> 4) + 16 m + (tid & 15)
+    for j in range(16):
+        for w in range(8):
+            lanes = range(32 * w, 32 * w + 32)
+            assert len({tphi(t + 256 * j) % 32 for t in lanes}) == 32
+            assert len({tphi(((t >> 4) << 8) + 16 * j + (t & 15)) % 32 for t in lanes}) == 32
+
+
+def test_tile_vector_pattern_conflict_free():
+    # stage C: residues 16 tid + 4 q read as 128-bit words
+    for q in range(4):
+        for t0 in range(0, 256, 8):
+            groups = [(tphi(16 * t + 4 * q) // 4) % 8 for t in range(t0, t0 + 8)]
+            assert len(set(groups)) == 8
+
+
+# -- one column per thread (k_colfwd / k_colinv) -----------------------------------
+
+def cphi(r, c):
+    return ((r ^ ((r >> 4) & 7)) << 2) | c
+
+
+@pytest.mark.parametrize("LF", [8, 9, 10, 11, 12])
+def test_one_column_layout_conflict_free(LF):
+    NT = (1 << LF) // 8
+    NST = (LF + 3) // 4
+    NL0 = LF - 4 * (NST - 1)
+    for S in range(NST):
+        NL = NL0 if S == 0 else 4
+        D0 = 0 if S == 0 else NL0 + 4 * (S - 1)
+        M, B, LST, LRB = 1 << NL, 16 >> NL, LF - D0 - NL, LF - D0
+        words = set()
+        for h in range(2 * B):
+            for i in range(M):
+                for w0 in range(0, NT, 32):
+                    banks = []
+                    for t in range(w0, min(w0 + 32, NT)):
+                        gg = t + NT * h
+                        col, g = gg & 3, gg >> 2
+                        blk = g >> LST
+                        row = (blk << LRB) + (g & ((1 << LST) - 1)) + (i << LST)
+                        banks.append(cphi(row, col) % 32)
+                        words.add(cphi(row, col))
+                    assert len(set(banks)) == len(banks)
+        assert words == set(range(4 << LF))
+
+
+# -- four columns per thread (k_colfwd4 / k_colinv4) ---------------------------------
+
+def c4_off16(LF, quad, row):
+    qs = ((quad & 3) << 1) | ((quad >> 2) & 1)
+    return (quad << LF) + (row ^ ((row >> 4) & 7) ^ qs)
+
+
+@pytest.mark.parametrize("LF", [8, 9, 10, 11, 12])
+def test_four_column_stages_conflict_free(LF):
+    NST = (LF + 3) // 4
+    NL0 = LF - 4 * (NST - 1)
+    for S in range(NST):
+        NL = NL0 if S == 0 else 4
+        D0 = 0 if S == 0 else NL0 + 4 * (S - 1)
+        M, B, LST, LRB, LGQ = 1 << NL, 16 >> NL, LF - D0 - NL, LF - D0, LF - NL
+        seen = set()
+        for h in range(B):
+            for i in range(M):
+                for t0 in range(0, 256, 8):
+                    groups = []
+                    for t in range(t0, t0 + 8):
+                        gg = t + 256 * h
+                        quad, g = gg >> LGQ, gg & ((1 << LGQ) - 1)
+                        blk = g >> LST
+                        row = (blk << LRB) + (g & ((1 << LST) - 1)) + (i << LST)
+                        groups.append(c4_off16(LF, quad, row) % 8)
+                        seen.add(c4_off16(LF, quad, row))
+                    assert len(set(groups)) == 8
+        assert seen == set(range(4096))
+
+
+@pytest.mark.parametrize("LF", [8, 9, 10, 11, 12])
+@pytest.mark.parametrize("maxlcl", [0, 1, 2, 3])
+def test_four_column_store_phase(LF, maxlcl):
+    """Each cluster rank's rows, every quad of the row segment: the words
+    covered once for every cluster size, and -- for the two-CTA clusters the
+    kernels are built with -- no two lanes of a phase in the same bank group
+    of one CTA's shared memory."""
+    LNQ = 12 - LF
+    LCL = min(0 if LNQ >= 3 else 3 - LNQ, maxlcl)
+    LCQ, LRW = LNQ + LCL, LF - LCL
+    RSTEP = 256 >> LCQ
+    cover = Counter()
+    for rank in range(1 << LCL):
+        for k in range(16):
+            for t0 in range(0, 256, 8):
+                per_cta = {}
+                for t in range(t0, t0 + 8):
+                    cq = t & ((1 << LCQ) - 1)
+                    row = (rank << LRW) + (t >> LCQ) + RSTEP * k
+                    cover[(cq, row)] += 1
+                    per_cta.setdefault(cq >> LNQ, []).append(c4_off16(LF, cq & ((1 << LNQ) - 1), row) % 8)
+                if maxlcl == 1:
+                    for groups in per_cta.values():
+                        assert len(set(groups)) == len(groups)
+    assert len(cover) == (1 << LCQ) << LF and set(cover.values()) == {1}
