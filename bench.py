@@ -228,7 +228,7 @@ def config_dict():
 #   k_colinv   3 x 24 + 21 = 93     (12 rec levels, CRT)
 MUL_SLOTS_PER_ELEM = {"k_colfwd": 138, "k_tile4096": 249, "k_colinv": 93}
 MUL_SLOTS_PER_ELEM["k_colfwd4"] = MUL_SLOTS_PER_ELEM["k_colfwd"]    # same pass, four columns per thread
-MUL_SLOTS_PER_ELEM["k_colinv4"] = MUL_SLOTS_PER_ELEM["k_colinv"]
+MUL_SLOTS_PER_ELEM["k_colinv4x3"] = MUL_SLOTS_PER_ELEM["k_colinv"]
 SLOTS_PER_SM_CYCLE = 4 * 16
 N_SMS = 152
 
@@ -242,7 +242,7 @@ def kernel_bytes():
         "k_tile4096": 6 * N * 4 + 3 * N * 4,
         "k_colinv": 3 * N * 4 + (2 * NPOLY - 1) * 8,
     }
-    b["k_colfwd4"], b["k_colinv4"] = b["k_colfwd"], b["k_colinv"]
+    b["k_colfwd4"], b["k_colinv4x3"] = b["k_colfwd"], b["k_colinv"]
     return b
 
 
@@ -252,12 +252,12 @@ def kernel_bytes():
 # changes the figure is stale and the bench reports null.  The summaries in
 # profiles/ give the commands and the other counters.
 _KSRC = {
-    "k_colfwd4": ["kernels_col4.cu", "tile_dev.cuh", "modarith.cuh", "kernels_mod.hpp"],
-    "k_colinv": ["kernels_fast.cu", "tile_dev.cuh", "modarith.cuh", "kernels_mod.hpp"],
+    "k_colfwd4": ["kernels_col4.cu", "cluster.cuh", "tile_dev.cuh", "modarith.cuh", "kernels_mod.hpp"],
+    "k_colinv4x3": ["kernels_col4.cu", "cluster.cuh", "tile_dev.cuh", "modarith.cuh", "kernels_mod.hpp"],
     "k_tile4096": ["kernels_fast.cu", "tile_dev.cuh", "modarith.cuh", "kernels_mod.hpp"],
 }
 NCU_TRAFFIC = {
-    "k_colfwd4": (381464576, "e92066b4bdc304f1"),
+    "k_tile4096": (568101120, "007434b1fe6d99c2"),
 }
 
 

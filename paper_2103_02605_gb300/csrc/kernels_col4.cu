@@ -35,6 +35,7 @@
 #include "common.hpp"
 #include "kernels_mod.hpp"
 #include "prof.hpp"
+#include "cluster.cuh"
 #include "tile_dev.cuh"
 
 namespace fcirc {
@@ -47,6 +48,9 @@ constexpr int kC4Threads = 256;
 // wider segments save.
 #ifndef FCIRC_C4_MAXLCL
 #define FCIRC_C4_MAXLCL 1
+#endif
+#ifndef FCIRC_C4_X3
+#define FCIRC_C4_X3 1
 #endif
 #ifndef FCIRC_C4FWD_MINB
 #define FCIRC_C4FWD_MINB 2
@@ -95,31 +99,6 @@ __device__ __forceinline__ int c4_off(int quad, int row)
 {
     const int qs = ((quad & 3) << 1) | ((quad >> 2) & 1);
     return (quad << (LF + 2)) + ((row ^ ((row >> 4) & 7) ^ qs) << 2);
-}
-
-// -- thread-block cluster primitives (distributed shared memory) --------------
-__device__ __forceinline__ void cl_arrive() { asm volatile("barrier.cluster.arrive.release.aligned;\n" ::: "memory"); }
-__device__ __forceinline__ void cl_wait() { asm volatile("barrier.cluster.wait.acquire.aligned;\n" ::: "memory"); }
-__device__ __forceinline__ uint32_t cl_rank()
-{
-    uint32_t r;
-    asm volatile("mov.u32 %0, %%cluster_ctarank;\n" : "=r"(r));
-    return r;
-}
-// address of the same shared-memory word in CTA `rank` of the cluster
-__device__ __forceinline__ uint32_t cl_map(uint32_t a, uint32_t rank)
-{
-    uint32_t r;
-    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;\n" : "=r"(r) : "r"(a), "r"(rank));
-    return r;
-}
-__device__ __forceinline__ uint4 cl_ld4(uint32_t a)
-{
-    uint4 v;
-    asm volatile("ld.shared::cluster.v4.u32 {%0, %1, %2, %3}, [%4];\n"
-                 : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
-                 : "r"(a));
-    return v;
 }
 
 // Barrier halves over the CTAs that share row segments (the cluster, or the
@@ -265,10 +244,11 @@ __device__ __forceinline__ void c4_fwd(uint32_t *v, const Tw *g, const Tw *cur, 
                 const int lo = (j << (NL - D)) + i;
 #pragma unroll
                 for (int c = 0; c < 4; ++c) {
+                    // the select form of the reduction measured faster here
                     if (VEC)
-                        bfly_vec(v[4 * lo + c], v[4 * (lo + h) + c], cur[j], p, p2);
+                        bfly_vec<false>(v[4 * lo + c], v[4 * (lo + h) + c], cur[j], p, p2);
                     else
-                        bfly_row(v[4 * lo + c], v[4 * (lo + h) + c], cur[j], p, p2);
+                        bfly_row<false>(v[4 * lo + c], v[4 * (lo + h) + c], cur[j], p, p2);
                 }
             }
         c4_fwd<NL, D + 1, VEC>(v, g, nxt, p, p2);
@@ -414,12 +394,13 @@ __device__ __forceinline__ void c4fwd_jobs(const ColFwdParams &P, uint32_t *sm, 
 
 // CTA origin: node pb of level l0 and the CTA's first column
 template <int LF>
-__device__ __forceinline__ void c4_origin(int logn, int l0, int l1, uint32_t &pb, uint32_t &base, int &logS)
+__device__ __forceinline__ void c4_origin(int logn, int l0, int l1, uint32_t &pb, uint32_t &base, int &logS,
+                                          uint32_t cta = blockIdx.x)
 {
     logS = logn - l1;
     const int cg_bits = logS - 2 - C4<LF>::LNQ;
-    pb = blockIdx.x >> cg_bits;
-    const uint32_t cg = blockIdx.x & ((1u << cg_bits) - 1);
+    pb = cta >> cg_bits;
+    const uint32_t cg = cta & ((1u << cg_bits) - 1);
     base = (pb << (logn - l0)) + (cg << (2 + C4<LF>::LNQ));
 }
 
@@ -438,19 +419,17 @@ __global__ void __cluster_dims__(C4<LF>::CL, 1, 1) __launch_bounds__(kC4Threads,
         c4fwd_jobs<LF, M1, true>(P, sm, j0, base, pb, logS, threadIdx.x);
 }
 
-template <int LF, int NP, int S>
-__device__ __forceinline__ void c4inv_stage(const ColInvParams &P, uint32_t *sm, uint32_t base, uint32_t pb,
-                                            int logS, int tid)
+// Stage S of the recombination for one prime's job J, its residues in smq.
+template <int LF, int S>
+__device__ __forceinline__ void c4inv_job(const ColInvParams &P, const ColInvJob &J, uint32_t *smq, uint32_t base,
+                                          uint32_t pb, int logS, int tid)
 {
     using Sh = C4<LF>;
     constexpr int NL = Sh::nl(S), D0 = Sh::d0(S);
     constexpr int M = 1 << NL, B = 16 >> NL, LST = LF - D0 - NL;
     constexpr bool FIRST = (S == Sh::NST - 1), LAST = (S == 0);
-#pragma unroll 1
-    for (int q = 0; q < NP; ++q) {
-        const ColInvJob &J = P.job[q];
+    {
         const uint32_t p = J.p, p2 = 2 * J.p;
-        uint32_t *smq = sm + q * Sh::WORDS;
         const Tw *gt = J.gitw + P.stage_off[S];
         uint32_t v[64];
 #pragma unroll
@@ -495,6 +474,14 @@ __device__ __forceinline__ void c4inv_stage(const ColInvParams &P, uint32_t *sm,
             }
         }
     }
+}
+
+template <int LF, int NP, int S>
+__device__ __forceinline__ void c4inv_stage(const ColInvParams &P, uint32_t *sm, uint32_t base, uint32_t pb,
+                                            int logS, int tid)
+{
+#pragma unroll 1
+    for (int q = 0; q < NP; ++q) c4inv_job<LF, S>(P, P.job[q], sm + q * C4<LF>::WORDS, base, pb, logS, tid);
 }
 
 // CRT phase of the polynomial product: the rows of the store phase, the three
@@ -560,6 +547,57 @@ __global__ void __cluster_dims__(C4<LF>::CL, 1, 1) __launch_bounds__(kC4Threads,
     grp_wait<Sh::CL>();
 }
 
+// Polynomial product, three primes: a cluster of three CTAs per column
+// group, CTA q running prime q's recombination levels in its own 64 KB of
+// shared memory (so two clusters' CTAs share an SM and overlap their memory
+// and arithmetic phases); then each CTA takes a third of the group's rows,
+// gathers the three canonical residues through distributed shared memory,
+// and writes the CRT result rotated by one (c_k = d_{k+1}).
+template <int LF>
+__global__ void __cluster_dims__(3, 1, 1) __launch_bounds__(kC4Threads, 2)
+    k_colinv4x3(const __grid_constant__ ColInvParams P)
+{
+    extern __shared__ __align__(16) uint32_t sm[];
+    using Sh = C4<LF>;
+    const int q = (int)cl_rank();
+    uint32_t pb, base;
+    int logS;
+    c4_origin<LF>(P.logn, P.l0, P.l1, pb, base, logS, blockIdx.x / 3);
+    const int tid = threadIdx.x;
+    const ColInvJob &J = P.job[q];
+    if constexpr (Sh::NST > 2) {
+        c4inv_job<LF, 2>(P, J, sm, base, pb, logS, tid);
+        __syncthreads();
+    }
+    if constexpr (Sh::NST > 1) {
+        c4inv_job<LF, 1>(P, J, sm, base, pb, logS, tid);
+        __syncthreads();
+    }
+    c4inv_job<LF, 0>(P, J, sm, base, pb, logS, tid);
+    cl_arrive();
+    cl_wait();   // all three primes' residues are in place
+    constexpr int W = 1 << 12;                   // 16-byte words (quad, row) per CTA
+    constexpr int W3 = (W + 2) / 3;
+    const int w0 = q * W3, w1 = (q + 1) * W3 < W ? (q + 1) * W3 : W;
+    const uint32_t own = smem_addr(sm);
+    const uint32_t s1 = cl_map(own, 0), s2 = cl_map(own, 1), s3 = cl_map(own, 2);
+    const uint32_t mask = P.N - 1;
+#pragma unroll 2
+    for (int w = w0 + tid; w < w1; w += kC4Threads) {
+        const int quad = w & ((1 << Sh::LNQ) - 1), row = w >> Sh::LNQ;
+        const uint32_t off = 4u * (uint32_t)c4_off<LF>(quad, row);
+        const uint4 r1 = cl_ld4(s1 + off), r2 = cl_ld4(s2 + off), r3 = cl_ld4(s3 + off);
+        const uint32_t idx = base + ((uint32_t)quad << 2) + ((uint32_t)row << logS);
+        const uint32_t d0 = (idx + mask) & mask;
+        if (d0 < P.nout) P.dst64[d0] = crt3(r1.x, r2.x, r3.x, P.crt);
+        if (idx < P.nout) P.dst64[idx] = crt3(r1.y, r2.y, r3.y, P.crt);
+        if (idx + 1 < P.nout) P.dst64[idx + 1] = crt3(r1.z, r2.z, r3.z, P.crt);
+        if (idx + 2 < P.nout) P.dst64[idx + 2] = crt3(r1.w, r2.w, r3.w, P.crt);
+    }
+    cl_arrive();
+    cl_wait();   // no CTA leaves while a peer still reads its shared memory
+}
+
 template <class K>
 int c4_smem(K kernel, int bytes, std::atomic<unsigned> &mask)
 {
@@ -618,6 +656,19 @@ int launch_c4inv_lf(const ColInvParams &P, cudaStream_t s)
     return FCIRC_OK;
 }
 
+template <int LF>
+int launch_c4inv_x3(const ColInvParams &P, cudaStream_t s)
+{
+    static std::atomic<unsigned> mask{0};
+    const int smem = C4<LF>::WORDS * 4;
+    FCIRC_TRY(c4_smem(k_colinv4x3<LF>, smem, mask));
+    const uint64_t ncta = (uint64_t)3 << (P.l0 + (P.logn - P.l1) - 2 - C4<LF>::LNQ);
+    ProfScope ps("k_colinv4x3", s);
+    k_colinv4x3<LF><<<(unsigned)ncta, kC4Threads, smem, s>>>(P);
+    FCIRC_CUDA_TRY(cudaGetLastError());
+    return FCIRC_OK;
+}
+
 }  // namespace
 
 // The pass can run here: LF in 8..12, enough columns for one cluster's
@@ -641,8 +692,8 @@ bool col4_inv_ok(const ColInvParams &P)
     const int lf = P.l1 - P.l0, logS = P.logn - P.l1;
     // every cluster's column groups lie in one level-l0 block
     if (lf < 8 || lf > 12 || logS < 2 + ((12 - lf) > 3 ? 12 - lf : 3)) return false;
-    // three primes: the one-column kernel (16 warps per SM) is faster
-    if (P.nprime != 1) return false;
+    // three primes only with the CRT epilogue (the three-CTA cluster kernel)
+    if (P.nprime != 1 && !(P.nprime == 3 && P.epi == EPI_CRT_ROT && FCIRC_C4_X3)) return false;
     for (int q = 0; q < P.nprime; ++q)
         if (!aligned(P.job[q].src, 16) || (P.epi != EPI_CRT_ROT && !aligned(P.job[q].dst, 16))) return false;
     return true;
@@ -679,13 +730,13 @@ int launch_colinv4(const ColInvParams &P, cudaStream_t s)
         case 11: return launch_c4inv_lf<11, 1>(P, s);
         case 12: return launch_c4inv_lf<12, 1>(P, s);
         }
-    } else if (P.nprime == 3) {
+    } else if (P.nprime == 3 && P.epi == EPI_CRT_ROT) {
         switch (lf) {
-        case 8: return launch_c4inv_lf<8, 3>(P, s);
-        case 9: return launch_c4inv_lf<9, 3>(P, s);
-        case 10: return launch_c4inv_lf<10, 3>(P, s);
-        case 11: return launch_c4inv_lf<11, 3>(P, s);
-        case 12: return launch_c4inv_lf<12, 3>(P, s);
+        case 8: return launch_c4inv_x3<8>(P, s);
+        case 9: return launch_c4inv_x3<9>(P, s);
+        case 10: return launch_c4inv_x3<10>(P, s);
+        case 11: return launch_c4inv_x3<11>(P, s);
+        case 12: return launch_c4inv_x3<12>(P, s);
         }
     }
     return fail(FCIRC_EINVAL, "column pass of %d levels, %d primes", lf, P.nprime);

@@ -46,15 +46,25 @@ FCIRC_HD uint32_t shoup_mul(uint32_t x, uint32_t w, uint32_t wp, uint32_t p)
     return x * w - q * p;
 }
 
-// x in [0, 2m) -> [0, m): min(x, x - m) in unsigned arithmetic (x - m wraps
-// to a large value when x < m)
-FCIRC_HD uint32_t reduce_once(uint32_t x, uint32_t m)
+// x in [0, 2m) -> [0, m).  Two instruction forms of the same result, chosen
+// per kernel by measurement: the select x >= m ? x - m : x, and
+// min(x, x - m) in unsigned arithmetic (x - m wraps to a large value when
+// x < m), which sm_103a issues as one add-and-min.
+FCIRC_HD uint32_t reduce_sel(uint32_t x, uint32_t m) { return x >= m ? x - m : x; }
+
+FCIRC_HD uint32_t reduce_min(uint32_t x, uint32_t m)
 {
-#if defined(__CUDA_ARCH__) && defined(FCIRC_REDUCE_MIN)
+#if defined(__CUDA_ARCH__)
     return umin(x, x - m);
 #else
     return x >= m ? x - m : x;
 #endif
+}
+
+template <bool UM = true>
+FCIRC_HD uint32_t reduce_once(uint32_t x, uint32_t m)
+{
+    return UM ? reduce_min(x, m) : reduce_sel(x, m);
 }
 
 // [0, 4p) -> [0, p)
@@ -119,21 +129,24 @@ FCIRC_HD Tw tw_neg(Tw t, uint32_t p)
 }
 
 // -- butterflies of Algorithm 1 ---------------------------------------------
+// UM selects the form of the conditional subtraction (see reduce_once).
 // Row-vector side (A_M1 / A_M2 rows):  (lo, hi) <- (lo + s hi, lo - s hi)
 // in/out range [0, 4p).
+template <bool UM = true>
 FCIRC_HD void bfly_row(uint32_t &lo, uint32_t &hi, Tw s, uint32_t p, uint32_t p2)
 {
     uint32_t t = shoup_mul(hi, s.w, s.wp, p);      // [0, 2p)
-    uint32_t l = reduce_once(lo, p2);              // [0, 2p)
+    uint32_t l = reduce_once<UM>(lo, p2);          // [0, 2p)
     lo = l + t;                                    // [0, 4p)
     hi = l - t + p2;                               // (0, 4p)
 }
 
 // Vector side: (lo, hi) <- (s lo + hi, s lo - hi); in/out range [0, 4p).
+template <bool UM = true>
 FCIRC_HD void bfly_vec(uint32_t &lo, uint32_t &hi, Tw s, uint32_t p, uint32_t p2)
 {
     uint32_t t = shoup_mul(lo, s.w, s.wp, p);      // [0, 2p)
-    uint32_t h = reduce_once(hi, p2);              // [0, 2p)
+    uint32_t h = reduce_once<UM>(hi, p2);          // [0, 2p)
     lo = t + h;
     hi = t - h + p2;
 }
