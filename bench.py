@@ -254,7 +254,7 @@ def kernel_bytes():
 _KSRC = {
     "k_colfwd4": ["kernels_col4.cu", "cluster.cuh", "tile_dev.cuh", "modarith.cuh", "kernels_mod.hpp"],
     "k_colinv4x3": ["kernels_col4.cu", "cluster.cuh", "tile_dev.cuh", "modarith.cuh", "kernels_mod.hpp"],
-    "k_tile4096": ["kernels_fast.cu", "tile_dev.cuh", "modarith.cuh", "kernels_mod.hpp"],
+    "k_tile4096": ["kernels_tile.cu", "tile_dev.cuh", "modarith.cuh", "kernels_mod.hpp"],
 }
 NCU_TRAFFIC = {
     "k_tile4096": (568101120, "007434b1fe6d99c2"),

@@ -8,56 +8,30 @@
 // stages the CTA re-distributes residues through shared memory, using
 // layouts chosen so that every warp access is free of bank conflicts.
 //
-//  * k_tile4096: one contiguous tile of 4096 residues (a node of level m-12)
-//    of one prime; halving levels 0-3 / 4-7 / 8-10 of the tile, the 2x2 leaf
-//    products, and the recombination back up.  Twiddles of levels 0-7 are
-//    generated once per CTA into shared memory, those of levels 8-10 by each
-//    thread for its own subtree (plan.cu explains the factorisation).
 //  * k_colfwd<LF> / k_colinv<LF, NP>: LF (8..12) top levels of the whole
-//    array, over 4 adjacent columns of 2^LF rows per CTA; the inverse pass
-//    can carry all three primes of a polynomial product and finish with the
-//    CRT.
+//    array, over 4 adjacent columns of 2^LF rows per CTA, one column per
+//    thread; the inverse pass can carry all three primes of a polynomial
+//    product and finish with the CRT.  The four-column kernels of
+//    kernels_col4.cu take the passes they accept; these take the rest.
 #include <atomic>
 
 #include "common.hpp"
 #include "kernels_mod.hpp"
 #include "prof.hpp"
-#include "cluster.cuh"
 #include "tile_dev.cuh"
 
 namespace fcirc {
 
-// ---------------------------------------------------------------------------
-// tile kernel, 4096 residues, 256 threads (the body is tile4096_dev)
-
-// Resident CTAs per SM the kernels are compiled for (register budgets).
-#ifndef FCIRC_TILE_MINB
-#define FCIRC_TILE_MINB 3
-#endif
+// Resident CTAs per SM the column kernels are compiled for (register budgets).
 #ifndef FCIRC_COL4
 #define FCIRC_COL4 1
 #endif
 #ifndef FCIRC_COLFWD_MINB
 #define FCIRC_COLFWD_MINB 2
 #endif
-#ifndef FCIRC_COLINV_PAIR
-#define FCIRC_COLINV_PAIR 1
-#endif
 #ifndef FCIRC_COLINV_MINB
 #define FCIRC_COLINV_MINB 2
 #endif
-
-template <int MA, int MX>
-__global__ void __launch_bounds__(256, FCIRC_TILE_MINB) k_tile4096(const __grid_constant__ TileParams P)
-{
-    __shared__ __align__(16) uint32_t SA[4096];
-    __shared__ __align__(16) uint32_t SX[4096];
-    __shared__ Tw STW[256];
-    __shared__ Tw SITW[256];
-    const TileJob &J = P.job[blockIdx.y];
-    const uint64_t t = blockIdx.x;
-    tile4096_dev<MA, MX>(J, (uint32_t)P.N, (uint32_t)(t << 12), J.sig + t * (uint64_t)(11 * 6), SA, SX, STW, SITW);
-}
 
 // ---------------------------------------------------------------------------
 // column passes: 2^LF rows x 4 adjacent columns per CTA, 2^LF / 8 threads,
@@ -279,16 +253,14 @@ __global__ void __launch_bounds__(ColShape<LF>::NT, FCIRC_COLFWD_MINB) k_colfwd(
         colfwd_jobs<LF, M1>(P, sm, j0, base, pb, logS, tid);
 }
 
-// GL: the first stage reads global memory (otherwise a cooperative load
-// phase has already put its input into shared memory)
-template <int LF, int NP, int S, bool GL = true>
+template <int LF, int NP, int S>
 __device__ __forceinline__ void colinv_stage(const ColInvParams &P, uint32_t *sm, uint32_t base,
                                              uint32_t pb, int logS, int tid)
 {
     using Sh = ColShape<LF>;
     constexpr int NL = Sh::nl(S), D0 = Sh::d0(S);
     constexpr int M = 1 << NL, B = 16 >> NL, LST = LF - D0 - NL;
-    constexpr bool FIRST = (S == Sh::NST - 1) && GL, LAST = (S == 0);
+    constexpr bool FIRST = (S == Sh::NST - 1), LAST = (S == 0);
     constexpr int R = 1 << LF;
 #pragma unroll 1
     for (int q = 0; q < NP; ++q) {
@@ -373,64 +345,6 @@ __global__ void __launch_bounds__(ColShape<LF>::NT, NP == 1 ? FCIRC_COLINV_MINB 
     colinv_stage<LF, NP, 0>(P, sm, base, pb, logS, tid);
 }
 
-// Inverse pass in CTA pairs (two-CTA clusters over adjacent column groups).
-// The first stage's input is read cooperatively: CTA k of the pair reads
-// rows [k R/2, (k+1) R/2) of the pair's 8 columns as 32-byte row segments
-// (two lanes each, whole DRAM sectors) and delivers each 16-byte half to the
-// shared memory of the CTA that owns those 4 columns; the one-CTA kernel
-// reads 16-byte segments, half sectors, which cost twice the L2 requests.
-template <int LF, int NP>
-__device__ __forceinline__ void colinv_pair_load(const ColInvParams &P, uint32_t *sm, uint32_t base0, int logS,
-                                                 int rank, int tid)
-{
-    using Sh = ColShape<LF>;
-    constexpr int R = 1 << LF, NT = Sh::NT, PER = R / NT;   // 8 segments per thread and prime
-    const int qd = tid & 1;
-    const int r0 = rank * (R / 2) + (tid >> 1);
-    const uint32_t dst = cl_map(smem_addr(sm), (uint32_t)qd);
-#pragma unroll 1
-    for (int q = 0; q < NP; ++q) {
-        const uint32_t *src = P.job[q].src + base0 + 4 * qd;
-        uint4 w[PER];
-#pragma unroll
-        for (int j = 0; j < PER; ++j) {
-            const uint32_t row = r0 + j * (NT / 2);
-            w[j] = __ldg(reinterpret_cast<const uint4 *>(src + (row << logS)));
-        }
-#pragma unroll
-        for (int j = 0; j < PER; ++j) {
-            const int row = r0 + j * (NT / 2);
-            cl_st4(dst + 4u * (uint32_t)(q * R * 4 + cphi(row, 0)), w[j]);
-        }
-    }
-}
-
-template <int LF, int NP>
-__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(ColShape<LF>::NT, NP == 1 ? FCIRC_COLINV_MINB : 1)
-    k_colinv2(const __grid_constant__ ColInvParams P)
-{
-    extern __shared__ __align__(16) uint32_t sm[];
-    using Sh = ColShape<LF>;
-    const int tid = threadIdx.x;
-    const int logS = P.logn - P.l1;
-    const int cg_bits = logS - 2;
-    const uint32_t pb = blockIdx.x >> cg_bits;
-    const uint32_t cg = blockIdx.x & ((1u << cg_bits) - 1);
-    const uint32_t base = (pb << (P.logn - P.l0)) + (cg << 2);
-    const int rank = (int)cl_rank();
-    static_assert(Sh::NST >= 2 && Sh::NST <= 3, "column pass of 5..12 levels");
-    colinv_pair_load<LF, NP>(P, sm, base - 4u * (uint32_t)rank, logS, rank, tid);
-    cl_arrive();
-    cl_wait();   // both CTAs' deliveries are visible
-    colinv_stage<LF, NP, Sh::NST - 1, false>(P, sm, base, pb, logS, tid);
-    __syncthreads();
-    if constexpr (Sh::NST > 2) {
-        colinv_stage<LF, NP, 1>(P, sm, base, pb, logS, tid);
-        __syncthreads();
-    }
-    colinv_stage<LF, NP, 0>(P, sm, base, pb, logS, tid);
-}
-
 // ---------------------------------------------------------------------------
 // launchers
 
@@ -446,29 +360,11 @@ static int ensure_smem_f(K kernel, int bytes, std::atomic<unsigned> &mask)
     return FCIRC_OK;
 }
 
-bool fast_tile_ok(int logT) { return logT == 12; }
 bool fast_col_ok(int lf, int logS) { return lf >= 8 && lf <= 12 && logS >= 2; }
 
 static int src_mode(const Src &s, int half)
 {
     return s.kind | (s.scaled ? 4 : 0) | (half << 3);
-}
-
-int launch_tile_fast(const TileParams &P, uint64_t ntiles, int njobs, cudaStream_t s)
-{
-    dim3 grid((unsigned)ntiles, njobs);
-    const int ma = src_mode(P.job[0].a, 0), mx = src_mode(P.job[0].x, 0);
-    ProfScope ps("k_tile4096", s);
-    if (ma == MODE_U32 && mx == MODE_U32)
-        k_tile4096<MODE_U32, MODE_U32><<<grid, 256, 0, s>>>(P);
-    else if (ma == MODE_U32_S && mx == MODE_U32)
-        k_tile4096<MODE_U32_S, MODE_U32><<<grid, 256, 0, s>>>(P);
-    else if (ma == MODE_REV_S && mx == MODE_U16)
-        k_tile4096<MODE_REV_S, MODE_U16><<<grid, 256, 0, s>>>(P);
-    else
-        return fail(FCIRC_EINVAL, "tile kernel: unsupported source modes %d/%d", ma, mx);
-    FCIRC_CUDA_TRY(cudaGetLastError());
-    return FCIRC_OK;
 }
 
 template <int LF, int M0, int M1>
@@ -518,27 +414,12 @@ int launch_colfwd(const ColFwdParams &P, int nctay, cudaStream_t s)
     }
 }
 
-static bool colinv_pair_ok(const ColInvParams &P)
-{
-    if (P.logn - P.l1 < 3) return false;   // a pair's column groups lie in one level-l0 block
-    for (int q = 0; q < P.nprime; ++q)
-        if ((reinterpret_cast<uintptr_t>(P.job[q].src) & 15) != 0) return false;
-    return true;
-}
-
 template <int LF, int NP>
 static int launch_colinv_lf(const ColInvParams &P, cudaStream_t s)
 {
-    static std::atomic<unsigned> mask{0}, mask2{0};
+    static std::atomic<unsigned> mask{0};
     const int smem = NP * (1 << LF) * 4 * 4;
     const uint64_t ncta = (uint64_t)1 << (P.l0 + (P.logn - P.l1) - 2);
-    if (FCIRC_COLINV_PAIR && colinv_pair_ok(P)) {
-        FCIRC_TRY(ensure_smem_f(k_colinv2<LF, NP>, smem, mask2));
-        ProfScope ps("k_colinv2", s);
-        k_colinv2<LF, NP><<<(unsigned)ncta, ColShape<LF>::NT, smem, s>>>(P);
-        FCIRC_CUDA_TRY(cudaGetLastError());
-        return FCIRC_OK;
-    }
     FCIRC_TRY(ensure_smem_f(k_colinv<LF, NP>, smem, mask));
     ProfScope ps("k_colinv", s);
     k_colinv<LF, NP><<<(unsigned)ncta, ColShape<LF>::NT, smem, s>>>(P);
