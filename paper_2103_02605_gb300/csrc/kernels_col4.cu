@@ -42,12 +42,22 @@ namespace fcirc {
 
 namespace {
 
-constexpr int kC4Threads = 256;
+// log2 rows per thread in a register stage (a thread holds 4 x 2^LR
+// residues); the CTA has 16384 / (4 2^LR) threads.
+#ifndef FCIRC_C4_LR
+#define FCIRC_C4_LR 4
+#endif
+constexpr int kC4LR = FCIRC_C4_LR;
+constexpr int kC4Rows = 1 << kC4LR;
+constexpr int kC4Threads = 4096 >> kC4LR;
 // Largest cluster, log2: two CTAs (32-byte row segments, whole DRAM sectors)
 // measured fastest; larger clusters pay more in cluster-wide waits than the
 // wider segments save.
 #ifndef FCIRC_C4_MAXLCL
 #define FCIRC_C4_MAXLCL 1
+#endif
+#ifndef FCIRC_C4_SPLITJOBS
+#define FCIRC_C4_SPLITJOBS 1
 #endif
 #ifndef FCIRC_C4_X3
 #define FCIRC_C4_X3 1
@@ -64,10 +74,10 @@ struct C4 {
     static constexpr int R = 1 << LF;
     static constexpr int LNQ = 12 - LF;            // log2 column quads per CTA
     static constexpr int WORDS = 1 << 14;          // residues per CTA and job
-    static constexpr int NST = (LF + 3) / 4;
-    static constexpr int NL0 = LF - 4 * (NST - 1); // the first stage takes the remainder
-    static constexpr int nl(int s) { return s == 0 ? NL0 : 4; }
-    static constexpr int d0(int s) { return s == 0 ? 0 : NL0 + 4 * (s - 1); }
+    static constexpr int NST = (LF + kC4LR - 1) / kC4LR;
+    static constexpr int NL0 = LF - kC4LR * (NST - 1); // the first stage takes the remainder
+    static constexpr int nl(int s) { return s == 0 ? NL0 : kC4LR; }
+    static constexpr int d0(int s) { return s == 0 ? 0 : NL0 + kC4LR * (s - 1); }
     // Clusters of CL CTAs over adjacent column groups make every row segment
     // of the coalesced store phase 2^LCQ quads (16 2^LCQ bytes) wide.
     static constexpr int LCL0 = LNQ >= 3 ? 0 : 3 - LNQ;
@@ -91,14 +101,14 @@ __device__ __forceinline__ void c4_group(int tid, int h, int &quad, int &row0, i
 }
 
 // Shared-memory word of (quad, row, column 0): 16-byte row segments, the row
-// permuted inside aligned groups of 8 by bits 4..6 of the row and by the
+// permuted inside aligned groups of 8 by bits LR..LR+2 of the row and by the
 // quad (its low three bits rotated), so that the 8 lanes of one 128-bit
 // access phase hit distinct banks in every stage and in the store phase.
 template <int LF>
 __device__ __forceinline__ int c4_off(int quad, int row)
 {
     const int qs = ((quad & 3) << 1) | ((quad >> 2) & 1);
-    return (quad << (LF + 2)) + ((row ^ ((row >> 4) & 7) ^ qs) << 2);
+    return (quad << (LF + 2)) + ((row ^ ((row >> kC4LR) & 7) ^ qs) << 2);
 }
 
 // Barrier halves over the CTAs that share row segments (the cluster, or the
@@ -163,7 +173,7 @@ __device__ __forceinline__ void c4_store_phase(const uint32_t *smq, uint32_t *ds
     uint4 *d = reinterpret_cast<uint4 *>(dst + base0 + ((uint32_t)cq << 2) + ((uint32_t)row_t << logS));
     const size_t dstep = (size_t)RSTEP << (logS - 2);   // in uint4
 #pragma unroll
-    for (int h = 0; h < 2; ++h) {
+    for (int h = 0; h < kC4Rows / 8; ++h) {
         uint4 w[8];
 #pragma unroll
         for (int k = 0; k < 8; ++k) w[k] = c4_seg_ld<LF>(sb, cq, row_t + RSTEP * (8 * h + k));
@@ -292,12 +302,12 @@ __device__ __forceinline__ void c4fwd_stage(const ColFwdJob &J, const ColFwdPara
 {
     using Sh = C4<LF>;
     constexpr int NL = Sh::nl(S), D0 = Sh::d0(S);
-    constexpr int M = 1 << NL, B = 16 >> NL, LST = LF - D0 - NL;
+    constexpr int M = 1 << NL, B = kC4Rows >> NL, LST = LF - D0 - NL;
     constexpr bool FIRST = (S == 0);
     constexpr int half = FIRST ? ((MODE >> 3) & 3) : 0;
     const uint32_t p = J.p, p2 = 2 * J.p;
     const Tw *gt = J.gtw + P.stage_off[S];
-    uint32_t v[64];
+    uint32_t v[4 * kC4Rows];
     // every load of the stage is issued before any arithmetic
 #pragma unroll
     for (int hb = 0; hb < B; ++hb) {
@@ -384,6 +394,10 @@ __device__ __forceinline__ void c4fwd_jobs(const ColFwdParams &P, uint32_t *sm, 
             __syncthreads();
             c4fwd_stage<LF, 2, MODE, VEC>(J, P, sm, base, pb, logS, tid, false);
         }
+        if constexpr (Sh::NST > 3) {
+            __syncthreads();
+            c4fwd_stage<LF, 3, MODE, VEC>(J, P, sm, base, pb, logS, tid, false);
+        }
         grp_arrive<Sh::CL>();
         grp_wait<Sh::CL>();
         c4_store_phase<LF>(sm, J.dst, base0, logS, rank, tid);
@@ -412,8 +426,9 @@ __global__ void __cluster_dims__(C4<LF>::CL, 1, 1) __launch_bounds__(kC4Threads,
     int logS;
     c4_origin<LF>(P.logn, P.l0, P.l1, pb, base, logS);
     const int j0 = blockIdx.y * P.jobs_per_cta;
-    // job group 0 is the row-vector side, group 1 the vector side
-    if (blockIdx.y == 0)
+    // the first half of the job groups is the row-vector side, the second
+    // half the vector side
+    if (blockIdx.y < gridDim.y / 2)
         c4fwd_jobs<LF, M0, false>(P, sm, j0, base, pb, logS, threadIdx.x);
     else
         c4fwd_jobs<LF, M1, true>(P, sm, j0, base, pb, logS, threadIdx.x);
@@ -426,12 +441,12 @@ __device__ __forceinline__ void c4inv_job(const ColInvParams &P, const ColInvJob
 {
     using Sh = C4<LF>;
     constexpr int NL = Sh::nl(S), D0 = Sh::d0(S);
-    constexpr int M = 1 << NL, B = 16 >> NL, LST = LF - D0 - NL;
+    constexpr int M = 1 << NL, B = kC4Rows >> NL, LST = LF - D0 - NL;
     constexpr bool FIRST = (S == Sh::NST - 1), LAST = (S == 0);
     {
         const uint32_t p = J.p, p2 = 2 * J.p;
         const Tw *gt = J.gitw + P.stage_off[S];
-        uint32_t v[64];
+        uint32_t v[4 * kC4Rows];
 #pragma unroll
         for (int hb = 0; hb < B; ++hb) {
             int quad, row0, blk;
@@ -499,7 +514,7 @@ __device__ __forceinline__ void c4_crt_phase(const ColInvParams &P, const uint32
     const uint32_t sb = c4_seg_base<LF>(sm, cq);
     constexpr uint32_t PB = 4u * Sh::WORDS;   // bytes per prime region
 #pragma unroll 2
-    for (int k = 0; k < 16; ++k) {
+    for (int k = 0; k < kC4Rows; ++k) {
         const int row = row_t + RSTEP * k;
         const uint4 r1 = c4_seg_ld<LF>(sb, cq, row);
         const uint4 r2 = c4_seg_ld<LF>(sb + PB, cq, row);
@@ -525,6 +540,10 @@ __global__ void __cluster_dims__(C4<LF>::CL, 1, 1) __launch_bounds__(kC4Threads,
     const int tid = threadIdx.x;
     const int rank = Sh::CL > 1 ? (int)cl_rank() : 0;
     const uint32_t base0 = base - ((uint32_t)rank << (2 + Sh::LNQ));
+    if constexpr (Sh::NST > 3) {
+        c4inv_stage<LF, NP, 3>(P, sm, base, pb, logS, tid);
+        __syncthreads();
+    }
     if constexpr (Sh::NST > 2) {
         c4inv_stage<LF, NP, 2>(P, sm, base, pb, logS, tid);
         __syncthreads();
@@ -565,6 +584,10 @@ __global__ void __cluster_dims__(3, 1, 1) __launch_bounds__(kC4Threads, 2)
     c4_origin<LF>(P.logn, P.l0, P.l1, pb, base, logS, blockIdx.x / 3);
     const int tid = threadIdx.x;
     const ColInvJob &J = P.job[q];
+    if constexpr (Sh::NST > 3) {
+        c4inv_job<LF, 3>(P, J, sm, base, pb, logS, tid);
+        __syncthreads();
+    }
     if constexpr (Sh::NST > 2) {
         c4inv_job<LF, 2>(P, J, sm, base, pb, logS, tid);
         __syncthreads();
@@ -626,9 +649,17 @@ int launch_c4fwd_m(const ColFwdParams &P, int nctay, cudaStream_t s)
     const int smem = C4<LF>::WORDS * 4;
     FCIRC_TRY(c4_smem(k_colfwd4<LF, M0, M1>, smem, mask));
     const uint64_t ncta = (uint64_t)1 << (P.l0 + (P.logn - P.l1) - 2 - C4<LF>::LNQ);
-    dim3 grid((unsigned)ncta, nctay);
+    // one job per CTA: more, shorter CTAs (the jobs of one group share only
+    // their source, which the L2 serves)
+    ColFwdParams P1 = P;
+    int ny = nctay;
+    if (FCIRC_C4_SPLITJOBS) {
+        ny = nctay * P.jobs_per_cta;
+        P1.jobs_per_cta = 1;
+    }
+    dim3 grid((unsigned)ncta, ny);
     ProfScope ps("k_colfwd4", s);
-    k_colfwd4<LF, M0, M1><<<grid, kC4Threads, smem, s>>>(P);
+    k_colfwd4<LF, M0, M1><<<grid, kC4Threads, smem, s>>>(P1);
     FCIRC_CUDA_TRY(cudaGetLastError());
     return FCIRC_OK;
 }
@@ -679,7 +710,7 @@ bool col4_fwd_ok(const ColFwdParams &P, int nctay)
     const int lf = P.l1 - P.l0, logS = P.logn - P.l1;
     // every cluster's column groups lie in one level-l0 block
     if (lf < 8 || lf > 12 || logS < 2 + ((12 - lf) > 3 ? 12 - lf : 3)) return false;
-    if (nctay > 2) return false;
+    if (nctay != 2) return false;   // one group per side
     for (int k = 0; k < nctay * P.jobs_per_cta; ++k)
         if (!src_aligned(P.job[k].src) || !aligned(P.job[k].dst, 16) ||
             P.job[k].vec_side != k / P.jobs_per_cta)

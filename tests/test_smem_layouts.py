@@ -75,56 +75,61 @@ def test_one_column_layout_conflict_free(LF):
 
 # -- four columns per thread (k_colfwd4 / k_colinv4) ---------------------------------
 
-def c4_off16(LF, quad, row):
+def c4_off16(LF, quad, row, LR=4):
     qs = ((quad & 3) << 1) | ((quad >> 2) & 1)
-    return (quad << LF) + (row ^ ((row >> 4) & 7) ^ qs)
+    return (quad << LF) + (row ^ ((row >> LR) & 7) ^ qs)
 
 
+@pytest.mark.parametrize("LR", [3, 4])
 @pytest.mark.parametrize("LF", [8, 9, 10, 11, 12])
-def test_four_column_stages_conflict_free(LF):
-    NST = (LF + 3) // 4
-    NL0 = LF - 4 * (NST - 1)
+def test_four_column_stages_conflict_free(LF, LR):
+    """2^LR rows x 4 columns per thread, 4096 / 2^LR threads."""
+    NT, ROWS = 4096 >> LR, 1 << LR
+    NST = (LF + LR - 1) // LR
+    NL0 = LF - LR * (NST - 1)
     for S in range(NST):
-        NL = NL0 if S == 0 else 4
-        D0 = 0 if S == 0 else NL0 + 4 * (S - 1)
-        M, B, LST, LRB, LGQ = 1 << NL, 16 >> NL, LF - D0 - NL, LF - D0, LF - NL
+        NL = NL0 if S == 0 else LR
+        D0 = 0 if S == 0 else NL0 + LR * (S - 1)
+        M, B, LST, LRB, LGQ = 1 << NL, ROWS >> NL, LF - D0 - NL, LF - D0, LF - NL
         seen = set()
         for h in range(B):
             for i in range(M):
-                for t0 in range(0, 256, 8):
+                for t0 in range(0, NT, 8):
                     groups = []
                     for t in range(t0, t0 + 8):
-                        gg = t + 256 * h
+                        gg = t + NT * h
                         quad, g = gg >> LGQ, gg & ((1 << LGQ) - 1)
                         blk = g >> LST
                         row = (blk << LRB) + (g & ((1 << LST) - 1)) + (i << LST)
-                        groups.append(c4_off16(LF, quad, row) % 8)
-                        seen.add(c4_off16(LF, quad, row))
+                        groups.append(c4_off16(LF, quad, row, LR) % 8)
+                        seen.add(c4_off16(LF, quad, row, LR))
                     assert len(set(groups)) == 8
         assert seen == set(range(4096))
 
 
+@pytest.mark.parametrize("LR", [3, 4])
 @pytest.mark.parametrize("LF", [8, 9, 10, 11, 12])
 @pytest.mark.parametrize("maxlcl", [0, 1, 2, 3])
-def test_four_column_store_phase(LF, maxlcl):
+def test_four_column_store_phase(LF, maxlcl, LR):
     """Each cluster rank's rows, every quad of the row segment: the words
     covered once for every cluster size, and -- for the two-CTA clusters the
     kernels are built with -- no two lanes of a phase in the same bank group
     of one CTA's shared memory."""
+    NT, ROWS = 4096 >> LR, 1 << LR
     LNQ = 12 - LF
     LCL = min(0 if LNQ >= 3 else 3 - LNQ, maxlcl)
     LCQ, LRW = LNQ + LCL, LF - LCL
-    RSTEP = 256 >> LCQ
+    RSTEP = NT >> LCQ
     cover = Counter()
     for rank in range(1 << LCL):
-        for k in range(16):
-            for t0 in range(0, 256, 8):
+        for k in range(ROWS):
+            for t0 in range(0, NT, 8):
                 per_cta = {}
                 for t in range(t0, t0 + 8):
                     cq = t & ((1 << LCQ) - 1)
                     row = (rank << LRW) + (t >> LCQ) + RSTEP * k
                     cover[(cq, row)] += 1
-                    per_cta.setdefault(cq >> LNQ, []).append(c4_off16(LF, cq & ((1 << LNQ) - 1), row) % 8)
+                    per_cta.setdefault(cq >> LNQ, []).append(c4_off16(LF, cq & ((1 << LNQ) - 1), row, LR) % 8)
                 if maxlcl == 1:
                     for groups in per_cta.values():
                         assert len(set(groups)) == len(groups)
