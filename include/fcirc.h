@@ -19,9 +19,14 @@
  *    allocation on the current device) or a HOST pointer (pageable or
  *    pinned).  The caller allocates and owns all of them; the library never
  *    frees or keeps them.  With device pointers only, the call enqueues its
- *    kernels on `stream` and returns without waiting.  If any array is in
- *    host memory, the call stages it through device memory on `stream` and
- *    returns after the results are back in the caller's buffers.
+ *    kernels on `stream` and returns without waiting.  Host arrays are
+ *    staged through device memory on `stream`.  If any of them is pageable,
+ *    the call returns after the results are back in the caller's buffers.
+ *    If all of them are page-locked (cudaHostAlloc / cudaHostRegister), the
+ *    call is asynchronous like cudaMemcpyAsync: it returns at once, host
+ *    inputs must stay unchanged and host outputs are valid only once
+ *    `stream` has passed the call (so independent products on two streams
+ *    overlap one's copies with the other's kernels).
  *  * stream: a cudaStream_t passed as void* (NULL = the legacy default
  *    stream) on the current device.
  *  * Scratch: kept in a per-device pool inside the library, grown on demand

@@ -6,6 +6,12 @@ computation runs in the library's CUDA kernels.  PyTorch provides device
 memory and streams.  If the shared library has not been built the calls
 raise; there is no fallback path.
 
+Tensors may live on the current CUDA device or in host memory.  With
+device tensors the calls only enqueue work on ``stream`` (default: torch's
+current stream).  With pageable host tensors they return when the results
+are in place; with pinned host tensors only they are asynchronous like
+``cudaMemcpyAsync`` -- synchronise ``stream`` before reading the outputs.
+
 Method: Rosowski, "On Fast Computation of a Circulant Matrix-Vector Product"
 (arXiv 2103.02605), Algorithm 1 / Theorem 1 (Section 2) and the
 applications of Section 3.

@@ -34,6 +34,7 @@ struct Arg {
     size_t bytes;
     bool in, out;
     bool on_device;
+    bool pinned;        // page-locked host memory
     void *d;            // device pointer used by the kernels
 };
 
@@ -41,6 +42,7 @@ int classify(Arg &a)
 {
     cudaPointerAttributes attr;
     cudaError_t e = cudaPointerGetAttributes(&attr, a.user);
+    a.pinned = false;
     if (e != cudaSuccess) {
         (void)cudaGetLastError();
         a.on_device = false;
@@ -55,6 +57,7 @@ int classify(Arg &a)
         a.on_device = true;
     } else {
         a.on_device = false;
+        a.pinned = attr.type == cudaMemoryTypeHost;
     }
     return FCIRC_OK;
 }
@@ -62,12 +65,15 @@ int classify(Arg &a)
 inline size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
 
 // Stages host arguments through the scratch pool; `extra` bytes of compute
-// scratch follow the staging area.
+// scratch follow the staging area.  With page-locked host buffers only, the
+// copies stay asynchronous on the stream (cudaMemcpyAsync semantics); any
+// pageable host buffer makes end() wait for the stream.
 struct Staging {
     std::vector<Arg *> args;
     cudaStream_t s;
     char *scratch = nullptr;
     bool any_host = false;
+    bool any_pageable = false;
 
     int begin(cudaStream_t st, size_t extra)
     {
@@ -77,6 +83,7 @@ struct Staging {
             FCIRC_TRY(classify(*a));
             if (!a->on_device) {
                 any_host = true;
+                any_pageable = any_pageable || !a->pinned;
                 need += align256(a->bytes);
             }
         }
@@ -105,7 +112,7 @@ struct Staging {
             if (!a->on_device && a->out && a->bytes)
                 FCIRC_CUDA_TRY(cudaMemcpyAsync(const_cast<void *>(a->user), a->d, a->bytes,
                                                cudaMemcpyDeviceToHost, s));
-        FCIRC_CUDA_TRY(cudaStreamSynchronize(s));
+        if (any_pageable) FCIRC_CUDA_TRY(cudaStreamSynchronize(s));
         return FCIRC_OK;
     }
 };

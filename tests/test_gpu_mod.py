@@ -198,6 +198,28 @@ def test_poly_host_buffers(F, orc):
     assert np.array_equal(out.numpy(), orc.poly_mul(Pc, Qc))
 
 
+def test_poly_pinned_buffers_async_on_two_streams(F, orc):
+    """Page-locked host buffers: the call is asynchronous on its stream, so
+    two products on two streams are in flight together; after both streams
+    finish, both outputs are exact."""
+    import torch
+    pairs = [I.poly_pair(70000, seed=91), I.poly_pair(40000, nq=50001, seed=92)]
+    streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+    outs = []
+    for (Pc, Qc), st in zip(pairs, streams):
+        Ph = torch.from_numpy(Pc.view(np.int16)).pin_memory()
+        Qh = torch.from_numpy(Qc.view(np.int16)).pin_memory()
+        Oh = torch.full((Pc.size + Qc.size - 1,), -1, dtype=torch.int64).pin_memory()
+        F.poly_mul_int(Ph, Qh, out=Oh, stream=st)
+        outs.append((Ph, Qh, Oh))
+    for st in streams:
+        st.synchronize()
+    for (Pc, Qc), (_, _, Oh) in zip(pairs, outs):
+        idx = np.unique(np.concatenate([np.arange(8), np.arange(Oh.numel() - 8, Oh.numel()),
+                                        np.random.default_rng(3).integers(0, Oh.numel(), 200)]))
+        assert np.array_equal(Oh.numpy()[idx], orc.poly_mul_coeffs(Pc, Qc, idx.astype(np.uint64)))
+
+
 def test_poly_errors(F):
     import torch
     L = F.load()
