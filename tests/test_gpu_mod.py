@@ -91,6 +91,39 @@ def test_matvec_large_sampled(F, orc, m, p):
     assert got.max() < p
 
 
+@pytest.mark.parametrize("m", [21, 22, 23])
+def test_matvec_column_pass_shapes(F, orc, m):
+    """n = 2^21 .. 2^23: column passes of 9, 10 and 11 levels (clusters of
+    two over 2^(12-LF) column quads per CTA), checked on sampled rows."""
+    n = 1 << m
+    a, x = I.single_mod(n, P1, seed=I.SEED_BASE + 300 + m)
+    f = f_with_root(P1, n, 11 * m)
+    got = matvec(F, P1, f, a, x)
+    rows = sample_rows(n, seed=m + 1)
+    assert np.array_equal(got[rows.astype(np.int64)], orc.fcirc_matvec_mod_rows(P1, f, a, x, rows))
+
+
+@pytest.mark.parametrize("m", [20, 24])
+def test_matvec_unaligned_views_take_the_one_column_kernels(F, orc, m):
+    """Sources and destination offset by one word (not 16-byte aligned): the
+    four-column kernels decline and the one-column kernels run instead."""
+    import torch
+    n = 1 << m
+    a, x = I.single_mod(n, P2, seed=I.SEED_BASE + 400 + m)
+    f = f_with_root(P2, n, m)
+    buf_a = torch.zeros(n + 1, dtype=torch.int32, device="cuda")
+    buf_x = torch.zeros(n + 1, dtype=torch.int32, device="cuda")
+    buf_c = torch.zeros(n + 1, dtype=torch.int32, device="cuda")
+    buf_a[1:] = dev_u32(a)
+    buf_x[1:] = dev_u32(x)
+    F.fcirc_matvec(P2, f, buf_a[1:], buf_x[1:], out=buf_c[1:])
+    torch.cuda.synchronize()
+    got = host_u32(buf_c[1:])
+    assert np.array_equal(got, matvec(F, P2, f, a, x))
+    rows = sample_rows(n, seed=m + 2)
+    assert np.array_equal(got[rows.astype(np.int64)], orc.fcirc_matvec_mod_rows(P2, f, a, x, rows))
+
+
 def test_matvec_config0_full(F, orc):
     """n = 2^12, f = 1, p = 998244353: the single-instance workload, full vector."""
     a, x = I.single_mod(1 << 12)
@@ -164,6 +197,38 @@ def poly(F, Pc, Qc):
 def test_poly_full(F, orc, np_, nq):
     Pc, Qc = I.poly_pair(np_, seed=np_ * 7 + nq, nq=nq)
     assert np.array_equal(poly(F, Pc, Qc), orc.poly_mul(Pc, Qc))
+
+
+@pytest.mark.parametrize("lg", [20, 21, 22])
+def test_poly_column_pass_shapes(F, orc, lg):
+    """Circulant sizes 2^21 .. 2^23 (column passes of 9 .. 11 levels with the
+    three-CTA inverse): sampled coefficients exactly, plus evaluation mod a
+    61-bit prime."""
+    n = 1 << lg
+    Pc, Qc = I.poly_pair(n, seed=I.SEED_BASE + 500 + lg, nq=n - 3)
+    C = poly(F, Pc, Qc)
+    rng = np.random.default_rng(lg)
+    idx = np.unique(np.concatenate([[0, 1, n - 1, n, C.size - 1],
+                                    rng.integers(0, C.size, 60)])).astype(np.uint64)
+    assert np.array_equal(C[idx.astype(np.int64)], orc.poly_mul_coeffs(Pc, Qc, idx))
+    q = (1 << 61) - 1
+    t = int(rng.integers(2, q))
+    assert orc.eval_i64_mod(C, t, q) == orc.eval_u16_mod(Pc, t, q) * orc.eval_u16_mod(Qc, t, q) % q
+
+
+def test_poly_unaligned_inputs(F, orc):
+    """uint16 inputs at odd element offsets: the forward pass falls back to
+    the one-column kernel; the result is unchanged."""
+    import torch
+    n = 1 << 22
+    Pc, Qc = I.poly_pair(n, seed=77)
+    bp = torch.zeros(n + 1, dtype=torch.int16, device="cuda")
+    bq = torch.zeros(n + 3, dtype=torch.int16, device="cuda")
+    bp[1:] = dev_u16(Pc)
+    bq[3:] = dev_u16(Qc)
+    C = F.poly_mul_int(bp[1:], bq[3:])
+    torch.cuda.synchronize()
+    assert np.array_equal(C.cpu().numpy(), poly(F, Pc, Qc))
 
 
 def test_poly_extreme_coefficients(F):
