@@ -106,6 +106,41 @@ int fcirc_matvec_noalloc(uint32_t p, uint32_t f, const uint32_t *a, const uint32
                          uint32_t *c, uint64_t n, void *stream);
 
 /*
+ * Fixed-matrix plans -- many products c = A x with the same f-circulant A.
+ *
+ * In Algorithm 1 (Section 2) the row vector's halvings (a_lo +- s a_hi down
+ * to the 2x2 leaves) do not depend on the vector: they are one of the three
+ * trees of the product.  A plan runs that tree once and keeps its result
+ * (n residues on the device), so each product with the plan runs only the
+ * vector tree, the leaf products and the recombination.  The paper has no
+ * plan object; this is the reuse its structure allows.
+ *
+ * fcirc_aplan_create
+ *   p, f, n   as for fcirc_matvec (the same errors for bad p, f, n).
+ *   a         uint32[n], the row vector, values < p; device or host memory.
+ *   stream    the row tree is computed on this stream; the plan is ready
+ *             once the stream has passed the call (use it on the same
+ *             stream, or synchronise first).
+ *   plan      receives the handle.  The plan owns n * 4 bytes of device
+ *             memory on the current device (FCIRC_ENOMEM if that fails).
+ *             For n < 4096 the plan keeps a itself and each product runs
+ *             in full.
+ * fcirc_matvec_aplan
+ *   c = A x for the plan's A: x, c uint32[n] as for fcirc_matvec (device
+ *   or host memory, same synchronisation rules), on `stream`, with the
+ *   plan's device current.  The result equals fcirc_matvec's exactly.
+ *   Calls with one plan may run concurrently (the plan is read only).
+ * fcirc_aplan_destroy
+ *   frees the plan (cudaFree, which waits for the device); NULL is a
+ *   no-op.  The caller makes sure no call using the plan is still running.
+ */
+typedef struct fcirc_aplan *fcirc_aplan_t;
+int fcirc_aplan_create(uint32_t p, uint32_t f, const uint32_t *a, uint64_t n, void *stream,
+                       fcirc_aplan_t *plan);
+int fcirc_matvec_aplan(fcirc_aplan_t plan, const uint32_t *x, uint32_t *c, void *stream);
+int fcirc_aplan_destroy(fcirc_aplan_t plan);
+
+/*
  * fcirc_matvec_batched -- many independent products c_i = A_i x_i over
  * Z/pZ (Algorithm 1 per instance), each with its own size and f, in one
  * persistent launch.

@@ -26,7 +26,7 @@ from . import build as _build
 
 __all__ = [
     "FcircError", "library_path", "load",
-    "fcirc_matvec", "fcirc_matvec_noalloc", "poly_mul_int", "bigint_mul",
+    "fcirc_matvec", "fcirc_matvec_noalloc", "APlan", "poly_mul_int", "bigint_mul",
     "fcirc_matvec_c64", "fcirc_matvec_backward", "fcirc_layer",
     "fcirc_matvec_batched", "batched_autotune", "BatchedGraph", "sync_status", "release",
     "nth_root", "node_twiddle", "leaf_param", "twiddle_from_factor",
@@ -45,6 +45,9 @@ _vp = ctypes.c_void_p
 _SIGNATURES = {
     "fcirc_matvec": ([_u32, _u32, _vp, _vp, _vp, _u64, _vp], _i32),
     "fcirc_matvec_noalloc": ([_u32, _u32, _vp, _vp, _vp, _u64, _vp], _i32),
+    "fcirc_aplan_create": ([_u32, _u32, _vp, _u64, _vp, ctypes.POINTER(_vp)], _i32),
+    "fcirc_matvec_aplan": ([_vp, _vp, _vp, _vp], _i32),
+    "fcirc_aplan_destroy": ([_vp], _i32),
     "poly_mul_int": ([_vp, _u64, _vp, _u64, _vp, _vp], _i32),
     "bigint_mul": ([_vp, _u64, _vp, _u64, _vp, _vp], _i32),
     "fcirc_matvec_c64": ([_vp, _vp, _vp, ctypes.c_double, ctypes.c_double, _u64, _u64, _vp], _i32),
@@ -159,6 +162,56 @@ def fcirc_matvec_noalloc(p: int, f: int, a, x, out, stream=None):
     _check(load().fcirc_matvec_noalloc(p, f % p, a.data_ptr(), x.data_ptr(), out.data_ptr(), a.numel(), st),
            "fcirc_matvec_noalloc")
     return out
+
+
+class APlan:
+    """A fixed f-circulant matrix for many products (include/fcirc.h,
+    fcirc_aplan_*): the row vector's tree of Algorithm 1 runs once here, and
+    each ``matvec`` runs the vector's tree, the leaves and the recombination.
+    ``a``: uint32 row vector (device or host tensor), values < p.  The plan
+    owns n * 4 bytes of device memory until ``destroy`` (or garbage
+    collection, or the end of a ``with`` block)."""
+
+    def __init__(self, p: int, f: int, a, stream=None):
+        _u32_tensor(a, "a")
+        if a.dim() != 1:
+            raise ValueError("a must be 1-D")
+        self.p, self.f, self.n = p, f % p, a.numel()
+        h = _vp()
+        _check(load().fcirc_aplan_create(p, f % p, a.data_ptr(), a.numel(), _stream_handle(stream, a),
+                                         ctypes.byref(h)), "fcirc_aplan_create")
+        self._h = h
+
+    def matvec(self, x, out=None, stream=None):
+        import torch
+        if self._h is None:
+            raise ValueError("plan destroyed")
+        _u32_tensor(x, "x")
+        if x.dim() != 1 or x.numel() != self.n:
+            raise ValueError(f"x must be 1-D of length {self.n}")
+        if out is None:
+            out = torch.empty_like(x)
+        _u32_tensor(out, "out")
+        st = _stream_handle(stream, x, out)
+        _check(load().fcirc_matvec_aplan(self._h, x.data_ptr(), out.data_ptr(), st), "fcirc_matvec_aplan")
+        return out
+
+    def destroy(self):
+        if getattr(self, "_h", None) is not None:
+            _check(load().fcirc_aplan_destroy(self._h), "fcirc_aplan_destroy")
+            self._h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.destroy()
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
 
 
 def poly_mul_int(P, Q, out=None, stream=None):

@@ -395,6 +395,153 @@ int fcirc_matvec(uint32_t p, uint32_t f, const uint32_t *a, const uint32_t *x, u
     return st.end();
 }
 
+// -- fixed-matrix plans ----------------------------------------------------------
+
+}  // extern "C"
+
+struct fcirc_aplan {
+    uint32_t p, f;
+    uint64_t n;
+    int dev;
+    const Plan *pl;     // nullptr when n == 1
+    uint32_t *ahat;     // transformed row vector (planned) or the row vector itself
+    bool planned;       // n >= 4096: products run two of the three trees
+};
+
+extern "C" {
+
+int fcirc_aplan_create(uint32_t p, uint32_t f, const uint32_t *a, uint64_t n, void *stream, fcirc_aplan_t *out)
+{
+    set_error("");
+    if (!out) return fail(FCIRC_EINVAL, "fcirc_aplan_create: null plan pointer");
+    *out = nullptr;
+    if (!a) return fail(FCIRC_EINVAL, "fcirc_aplan_create: null pointer");
+    if (!is_pow2(n)) return fail(FCIRC_EINVAL, "fcirc_aplan_create: n = %llu is not a power of two",
+                                 (unsigned long long)n);
+    if (n > ((uint64_t)1 << kMaxLogN)) return fail(FCIRC_EINVAL, "fcirc_aplan_create: n above 2^%d", kMaxLogN);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const Plan *pl = nullptr;
+    if (n == 1) {
+        const PrimeTables *pt;
+        FCIRC_TRY(prime_tables(p, &pt));
+        if (f % p == 0) return fail(FCIRC_ENOROOT, "f = 0 has no inverse (Theorem 1)");
+    } else {
+        FCIRC_TRY(get_plan(p, f, n, &pl));
+    }
+    int dev = 0;
+    FCIRC_CUDA_TRY(cudaGetDevice(&dev));
+    void *mem = nullptr;
+    if (cudaMalloc(&mem, n * 4) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return fail(FCIRC_ENOMEM, "fcirc_aplan_create: %llu bytes of device memory", (unsigned long long)(n * 4));
+    }
+    fcirc_aplan *h = new fcirc_aplan{p, f % p, n, dev, pl, static_cast<uint32_t *>(mem), false};
+    auto undo = [&](int st) {
+        cudaFree(mem);
+        delete h;
+        return st;
+    };
+    Arg aa{a, n * 4, true, false};
+    Staging st;
+    st.args = {&aa};
+    int rc = st.begin(s, 0);
+    if (rc != FCIRC_OK) return undo(rc);
+    const uint32_t *da = static_cast<const uint32_t *>(aa.d);
+    h->planned = pl && pl->logT == 12;
+    if (!h->planned) {
+        if (cudaMemcpyAsync(h->ahat, da, n * 4, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+            return undo(fail(FCIRC_ECUDA, "fcirc_aplan_create: copy of the row vector"));
+    } else {
+        // the row vector's tree: the forward column passes of the row side,
+        // then the tiles' row levels (scaled by 2^32 2^-L on the first load)
+        const Src sa{da, n, SRC_U32, 1, pl->kt};
+        for (int i = 0; i < pl->npass; ++i) {
+            FwdDesc jd[1] = {FwdDesc{i == 0 ? sa : src_u32(h->ahat, n), h->ahat, pl, 0, 0}};
+            rc = run_fwd_pass(i, jd, 1, 1, s);
+            if (rc != FCIRC_OK) return undo(rc);
+        }
+        TileParams tp;
+        tp.job[0] = tile_job(pl, pl->k == 0 ? sa : src_u32(h->ahat, n), src_u32(h->ahat, n), h->ahat, 1);
+        tp.N = n;
+        tp.logT = pl->logT;
+        tp.D = pl->D;
+        tp.var = TILE_ROW;
+        rc = run_tile(tp, (uint64_t)1 << pl->k, 1, s);
+        if (rc != FCIRC_OK) return undo(rc);
+    }
+    rc = st.end();
+    if (rc != FCIRC_OK) return undo(rc);
+    *out = h;
+    return FCIRC_OK;
+}
+
+int fcirc_matvec_aplan(fcirc_aplan_t h, const uint32_t *x, uint32_t *c, void *stream)
+{
+    set_error("");
+    if (!h) return fail(FCIRC_EINVAL, "fcirc_matvec_aplan: null plan");
+    if (!x || !c) return fail(FCIRC_EINVAL, "fcirc_matvec_aplan: null pointer");
+    int dev = 0;
+    FCIRC_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev != h->dev)
+        return fail(FCIRC_EINVAL, "fcirc_matvec_aplan: plan lives on device %d, current device is %d", h->dev, dev);
+    if (!h->planned) return fcirc_matvec(h->p, h->f, h->ahat, x, c, h->n, stream);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const uint64_t n = h->n;
+    const Plan *pl = h->pl;
+    Arg ax{x, n * 4, true, false}, ac{c, n * 4, false, true};
+    Staging st;
+    st.args = {&ax, &ac};
+    FCIRC_TRY(st.begin(s, pl->k > 0 ? n * 4 : 0));
+    const uint32_t *dx = static_cast<const uint32_t *>(ax.d);
+    uint32_t *dc = static_cast<uint32_t *>(ac.d);
+    const Src sx = src_u32(dx, n), sah = src_u32(h->ahat, n);
+    if (pl->k == 0) {
+        TileParams tp;
+        tp.job[0] = tile_job(pl, sah, sx, dc, 0);
+        tp.N = n;
+        tp.logT = pl->logT;
+        tp.D = pl->D;
+        tp.var = TILE_PLANNED;
+        FCIRC_TRY(run_tile(tp, 1, 1, s));
+        return st.end();
+    }
+    // the vector's tree in the scratch, the tiles (transformed row vector
+    // read as it is) in place there, and the recombination into c
+    uint32_t *xs = reinterpret_cast<uint32_t *>(st.scratch);
+    for (int i = 0; i < pl->npass; ++i) {
+        FwdDesc jd[1] = {FwdDesc{i == 0 ? sx : src_u32(xs, n), xs, pl, 1, 0}};
+        FCIRC_TRY(run_fwd_pass(i, jd, 1, 1, s));
+    }
+    {
+        TileParams tp;
+        tp.job[0] = tile_job(pl, sah, src_u32(xs, n), xs, 1);
+        tp.N = n;
+        tp.logT = pl->logT;
+        tp.D = pl->D;
+        tp.var = TILE_PLANNED;
+        FCIRC_TRY(run_tile(tp, (uint64_t)1 << pl->k, 1, s));
+    }
+    for (int i = pl->npass - 1; i >= 0; --i) {
+        InvDesc jd[1] = {InvDesc{xs, i == 0 ? dc : xs, pl}};
+        FCIRC_TRY(run_inv_pass(i, jd, 1, i == 0 ? EPI_CANON : EPI_LAZY, nullptr, 0, nullptr, s));
+    }
+    return st.end();
+}
+
+int fcirc_aplan_destroy(fcirc_aplan_t h)
+{
+    set_error("");
+    if (!h) return FCIRC_OK;
+    int cur = 0;
+    FCIRC_CUDA_TRY(cudaGetDevice(&cur));
+    if (cur != h->dev) FCIRC_CUDA_TRY(cudaSetDevice(h->dev));
+    const cudaError_t e = cudaFree(h->ahat);
+    if (cur != h->dev) (void)cudaSetDevice(cur);
+    delete h;
+    if (e != cudaSuccess) return fail(FCIRC_ECUDA, "fcirc_aplan_destroy: %s", cudaGetErrorString(e));
+    return FCIRC_OK;
+}
+
 int poly_mul_int(const uint16_t *P, uint64_t np, const uint16_t *Q, uint64_t nq, int64_t *out,
                  void *stream)
 {

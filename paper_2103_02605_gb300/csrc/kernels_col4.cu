@@ -426,9 +426,9 @@ __global__ void __cluster_dims__(C4<LF>::CL, 1, 1) __launch_bounds__(kC4Threads,
     int logS;
     c4_origin<LF>(P.logn, P.l0, P.l1, pb, base, logS);
     const int j0 = blockIdx.y * P.jobs_per_cta;
-    // the first half of the job groups is the row-vector side, the second
-    // half the vector side
-    if (blockIdx.y < gridDim.y / 2)
+    // job groups below vec_group0 are the row-vector side, the rest the
+    // vector side
+    if ((int)blockIdx.y < P.vec_group0)
         c4fwd_jobs<LF, M0, false>(P, sm, j0, base, pb, logS, threadIdx.x);
     else
         c4fwd_jobs<LF, M1, true>(P, sm, j0, base, pb, logS, threadIdx.x);
@@ -655,6 +655,7 @@ int launch_c4fwd_m(const ColFwdParams &P, int nctay, cudaStream_t s)
     int ny = nctay;
     if (FCIRC_C4_SPLITJOBS) {
         ny = nctay * P.jobs_per_cta;
+        P1.vec_group0 = P.vec_group0 * P.jobs_per_cta;
         P1.jobs_per_cta = 1;
     }
     dim3 grid((unsigned)ncta, ny);
@@ -710,11 +711,13 @@ bool col4_fwd_ok(const ColFwdParams &P, int nctay)
     const int lf = P.l1 - P.l0, logS = P.logn - P.l1;
     // every cluster's column groups lie in one level-l0 block
     if (lf < 8 || lf > 12 || logS < 2 + ((12 - lf) > 3 ? 12 - lf : 3)) return false;
-    if (nctay != 2) return false;   // one group per side
-    for (int k = 0; k < nctay * P.jobs_per_cta; ++k)
-        if (!src_aligned(P.job[k].src) || !aligned(P.job[k].dst, 16) ||
-            P.job[k].vec_side != k / P.jobs_per_cta)
-            return false;
+    // at most one job group per side, the row-vector side first
+    if (nctay < 1 || nctay > 2) return false;
+    for (int k = 0; k < nctay * P.jobs_per_cta; ++k) {
+        const ColFwdJob &J = P.job[k], &J0 = P.job[(k / P.jobs_per_cta) * P.jobs_per_cta];
+        if (!src_aligned(J.src) || !aligned(J.dst, 16) || J.vec_side != J0.vec_side) return false;
+    }
+    if (nctay == 2 && !(P.job[0].vec_side == 0 && P.job[P.jobs_per_cta].vec_side == 1)) return false;
     return true;
 }
 
@@ -730,14 +733,20 @@ bool col4_inv_ok(const ColInvParams &P)
     return true;
 }
 
-int launch_colfwd4(const ColFwdParams &P, int nctay, cudaStream_t s)
+int launch_colfwd4(const ColFwdParams &Pin, int nctay, cudaStream_t s)
 {
-    const int m0 = c4_mode(P.job[0].src, P.job[0].half);
-    const int m1 = nctay > 1 ? c4_mode(P.job[P.jobs_per_cta].src, P.job[P.jobs_per_cta].half) : MODE_U32;
+    ColFwdParams P = Pin;
+    P.vec_group0 = 0;
+    while (P.vec_group0 < nctay && P.job[P.vec_group0 * P.jobs_per_cta].vec_side == 0) ++P.vec_group0;
+    // source mode of the row-vector group and of the vector group (when present)
+    const int m0 = P.vec_group0 > 0 ? c4_mode(P.job[0].src, P.job[0].half) : MODE_U32;
+    const int m1 = P.vec_group0 < nctay
+                       ? c4_mode(P.job[P.vec_group0 * P.jobs_per_cta].src, P.job[P.vec_group0 * P.jobs_per_cta].half)
+                       : MODE_U32;
     for (int g = 0; g < nctay; ++g)
         for (int k = 0; k < P.jobs_per_cta; ++k) {
             const ColFwdJob &J = P.job[g * P.jobs_per_cta + k];
-            if (c4_mode(J.src, J.half) != (g == 0 ? m0 : m1))
+            if (c4_mode(J.src, J.half) != (g < P.vec_group0 ? m0 : m1))
                 return fail(FCIRC_EINVAL, "column pass: mixed source modes in one job group");
         }
     switch (P.l1 - P.l0) {

@@ -35,10 +35,19 @@ struct TileJob {
     int store_lazy;
 };
 
+// What a 4096-residue tile computes.  TILE_FULL: both trees, the leaves and
+// the recombination.  TILE_ROW: the row-vector tree only; J.dst receives the
+// transformed row vector (the leaf operands of Algorithm 1's row side, lazy
+// in [0, 4p)) for reuse with many vectors.  TILE_PLANNED: J.a is such a
+// transformed row vector (read as it is); the vector tree, the leaves and
+// the recombination.
+enum : int { TILE_FULL = 0, TILE_ROW = 1, TILE_PLANNED = 2 };
+
 struct TileParams {
     TileJob job[3];
     uint64_t N;
     int logT, D;
+    int var = 0;           // TILE_FULL / TILE_ROW / TILE_PLANNED (tile_dev.cuh); logT = 12 only
 };
 
 struct StrFwdJob {
@@ -119,6 +128,7 @@ struct ColFwdJob {
 struct ColFwdParams {
     ColFwdJob job[6];
     int jobs_per_cta;      // 1, or 3 for the three primes of one side of a product
+    int vec_group0;        // job groups [0, vec_group0) are row-vector side (set by the launcher)
     uint32_t N;
     int logn, l0, l1;
     int stage_off[3];

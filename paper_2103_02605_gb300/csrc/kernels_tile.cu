@@ -20,7 +20,7 @@ namespace fcirc {
 #define FCIRC_TILE_MINB 3
 #endif
 
-template <int MA, int MX>
+template <int MA, int MX, int VAR = TILE_FULL>
 __global__ void __launch_bounds__(256, FCIRC_TILE_MINB) k_tile4096(const __grid_constant__ TileParams P)
 {
     __shared__ __align__(16) uint32_t SA[4096];
@@ -29,7 +29,8 @@ __global__ void __launch_bounds__(256, FCIRC_TILE_MINB) k_tile4096(const __grid_
     __shared__ Tw SITW[256];
     const TileJob &J = P.job[blockIdx.y];
     const uint64_t t = blockIdx.x;
-    tile4096_dev<MA, MX>(J, (uint32_t)P.N, (uint32_t)(t << 12), J.sig + t * (uint64_t)(11 * 6), SA, SX, STW, SITW);
+    tile4096_dev<MA, MX, VAR>(J, (uint32_t)P.N, (uint32_t)(t << 12), J.sig + t * (uint64_t)(11 * 6), SA, SX, STW,
+                              SITW);
 }
 
 bool fast_tile_ok(int logT) { return logT == 12; }
@@ -39,6 +40,32 @@ int launch_tile_fast(const TileParams &P, uint64_t ntiles, int njobs, cudaStream
     dim3 grid((unsigned)ntiles, njobs);
     const int ma = P.job[0].a.kind | (P.job[0].a.scaled ? 4 : 0);
     const int mx = P.job[0].x.kind | (P.job[0].x.scaled ? 4 : 0);
+    if (P.var == TILE_ROW) {
+        // the row-vector tree only: writes the transformed row vector
+        for (int k = 0; k < njobs; ++k)
+            if ((reinterpret_cast<uintptr_t>(P.job[k].dst) & 15) != 0)
+                return fail(FCIRC_EINVAL, "tile kernel: unaligned transformed row vector");
+        ProfScope ps("k_tile4096_row", s);
+        if (ma == MODE_U32)
+            k_tile4096<MODE_U32, MODE_U32, TILE_ROW><<<grid, 256, 0, s>>>(P);
+        else if (ma == MODE_U32_S)
+            k_tile4096<MODE_U32_S, MODE_U32, TILE_ROW><<<grid, 256, 0, s>>>(P);
+        else
+            return fail(FCIRC_EINVAL, "tile kernel: unsupported row source mode %d", ma);
+        FCIRC_CUDA_TRY(cudaGetLastError());
+        return FCIRC_OK;
+    }
+    if (P.var == TILE_PLANNED) {
+        // a transformed row vector (read as it is) with a vector
+        for (int k = 0; k < njobs; ++k)
+            if ((reinterpret_cast<uintptr_t>(P.job[k].a.ptr) & 15) != 0)
+                return fail(FCIRC_EINVAL, "tile kernel: unaligned transformed row vector");
+        if (mx != MODE_U32) return fail(FCIRC_EINVAL, "tile kernel: unsupported vector source mode %d", mx);
+        ProfScope ps("k_tile4096_planned", s);
+        k_tile4096<MODE_U32, MODE_U32, TILE_PLANNED><<<grid, 256, 0, s>>>(P);
+        FCIRC_CUDA_TRY(cudaGetLastError());
+        return FCIRC_OK;
+    }
     ProfScope ps("k_tile4096", s);
     if (ma == MODE_U32 && mx == MODE_U32)
         k_tile4096<MODE_U32, MODE_U32><<<grid, 256, 0, s>>>(P);

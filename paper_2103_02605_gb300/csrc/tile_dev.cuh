@@ -91,6 +91,28 @@ __device__ __forceinline__ void fwd2(uint32_t *a, uint32_t *x, TwFn tw, uint32_t
     }
 }
 
+// forward levels of one side only (VEC: the vector side)
+template <int NL, int NLEV, bool VEC, class TwFn>
+__device__ __forceinline__ void fwd1(uint32_t *v, TwFn tw, uint32_t p, uint32_t p2)
+{
+#pragma unroll
+    for (int d = 0; d < NLEV; ++d) {
+        const int h = (1 << NL) >> (d + 1);
+#pragma unroll
+        for (int j = 0; j < (1 << d); ++j) {
+            const Tw s = tw(d, j);
+#pragma unroll
+            for (int i = 0; i < h; ++i) {
+                const int lo = (j << (NL - d)) + i;
+                if (VEC)
+                    bfly_vec(v[lo], v[lo + h], s, p, p2);
+                else
+                    bfly_row(v[lo], v[lo + h], s, p, p2);
+            }
+        }
+    }
+}
+
 // recombination, local levels NLEV-1 .. 0
 template <int NL, int NLEV, class TwFn>
 __device__ __forceinline__ void rec1(uint32_t *v, TwFn tw, uint32_t p, uint32_t p2)
@@ -128,10 +150,11 @@ __device__ __forceinline__ int tphi(int e)
 // tile's first index in arrays of length N; sg its 11 levels of factors
 // (6 words each, see plan.cu); SA, SX (4096 words each, 16-byte aligned),
 // STW, SITW (256 entries) are this CTA's shared memory.  256 threads.
-template <int MA, int MX>
+template <int MA, int MX, int VAR = TILE_FULL>
 __device__ __forceinline__ void tile4096_dev(const TileJob &J, uint32_t N, uint32_t base, const uint32_t *sg,
                                              uint32_t *SA, uint32_t *SX, Tw *STW, Tw *SITW)
 {
+    constexpr bool DO_A = VAR != TILE_PLANNED, DO_X = VAR != TILE_ROW;
     const uint32_t p = J.p, p2 = 2 * J.p, pinv = J.pinv;
     const int tid = threadIdx.x;
 
@@ -140,52 +163,68 @@ __device__ __forceinline__ void tile4096_dev(const TileJob &J, uint32_t N, uint3
         const int d = 31 - __clz(tid);
         const uint32_t *e = sg + d * 6;
         STW[tid] = twiddle_from(J.U[tid], e[0], e[1], e[2], p);
-        SITW[tid] = twiddle_from(J.Ui[tid], e[3], e[4], e[5], p);
+        if (VAR != TILE_ROW) SITW[tid] = twiddle_from(J.Ui[tid], e[3], e[4], e[5], p);
     }
     uint32_t a[16], x[16];
 #pragma unroll
     for (int j = 0; j < 16; ++j) {
-        a[j] = ld_raw<MA>(J.a, N, base + tid + 256 * j);
-        x[j] = ld_raw<MX>(J.x, N, base + tid + 256 * j);
+        if (DO_A) a[j] = ld_raw<MA>(J.a, N, base + tid + 256 * j);
+        if (DO_X) x[j] = ld_raw<MX>(J.x, N, base + tid + 256 * j);
     }
 #pragma unroll
     for (int j = 0; j < 16; ++j) {
-        a[j] = ld_scale<MA>(a[j], J.a, p);
-        x[j] = ld_scale<MX>(x[j], J.x, p);
+        if (DO_A) a[j] = ld_scale<MA>(a[j], J.a, p);
+        if (DO_X) x[j] = ld_scale<MX>(x[j], J.x, p);
     }
     __syncthreads();
 
     // stage A: tile levels 0..3, residues tid + 256 j
-    fwd2<4, 4>(a, x, [&](int d, int j) { return STW[(1 << d) + j]; }, p, p2);
+    auto twA = [&](int d, int j) { return STW[(1 << d) + j]; };
+    if (DO_A && DO_X)
+        fwd2<4, 4>(a, x, twA, p, p2);
+    else if (DO_A)
+        fwd1<4, 4, false>(a, twA, p, p2);
+    else
+        fwd1<4, 4, true>(x, twA, p, p2);
 #pragma unroll
     for (int j = 0; j < 16; ++j) {
-        SA[tphi(tid + 256 * j)] = a[j];
-        SX[tphi(tid + 256 * j)] = x[j];
+        if (DO_A) SA[tphi(tid + 256 * j)] = a[j];
+        if (DO_X) SX[tphi(tid + 256 * j)] = x[j];
     }
     __syncthreads();
     // stage B: levels 4..7, residues 256 (tid >> 4) + 16 m + (tid & 15)
     const int eb = ((tid >> 4) << 8) + (tid & 15);
 #pragma unroll
     for (int m = 0; m < 16; ++m) {
-        a[m] = SA[tphi(eb + 16 * m)];
-        x[m] = SX[tphi(eb + 16 * m)];
+        if (DO_A) a[m] = SA[tphi(eb + 16 * m)];
+        if (DO_X) x[m] = SX[tphi(eb + 16 * m)];
     }
     const int nb = tid >> 4;
-    fwd2<4, 4>(a, x, [&](int d, int j) { return STW[(1 << (4 + d)) + (nb << d) + j]; }, p, p2);
+    auto twB = [&](int d, int j) { return STW[(1 << (4 + d)) + (nb << d) + j]; };
+    if (DO_A && DO_X)
+        fwd2<4, 4>(a, x, twB, p, p2);
+    else if (DO_A)
+        fwd1<4, 4, false>(a, twB, p, p2);
+    else
+        fwd1<4, 4, true>(x, twB, p, p2);
     __syncthreads();
 #pragma unroll
     for (int m = 0; m < 16; ++m) {
-        SA[tphi(eb + 16 * m)] = a[m];
-        SX[tphi(eb + 16 * m)] = x[m];
+        if (DO_A) SA[tphi(eb + 16 * m)] = a[m];
+        if (DO_X) SX[tphi(eb + 16 * m)] = x[m];
     }
     __syncthreads();
     // stage C: levels 8..10 and the leaves, residues 16 tid .. 16 tid + 15
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-        const uint4 va = *reinterpret_cast<const uint4 *>(&SA[tphi(16 * tid + 4 * q)]);
-        const uint4 vx = *reinterpret_cast<const uint4 *>(&SX[tphi(16 * tid + 4 * q)]);
-        a[4 * q] = va.x; a[4 * q + 1] = va.y; a[4 * q + 2] = va.z; a[4 * q + 3] = va.w;
-        x[4 * q] = vx.x; x[4 * q + 1] = vx.y; x[4 * q + 2] = vx.z; x[4 * q + 3] = vx.w;
+        if (DO_A) {
+            const uint4 va = *reinterpret_cast<const uint4 *>(&SA[tphi(16 * tid + 4 * q)]);
+            a[4 * q] = va.x; a[4 * q + 1] = va.y; a[4 * q + 2] = va.z; a[4 * q + 3] = va.w;
+        }
+        if (DO_X) {
+            const uint4 vx = *reinterpret_cast<const uint4 *>(&SX[tphi(16 * tid + 4 * q)]);
+            x[4 * q] = vx.x; x[4 * q + 1] = vx.y; x[4 * q + 2] = vx.z; x[4 * q + 3] = vx.w;
+        }
     }
     Tw tc[7];   // this thread's nodes: level 8 (tid), 9 (2 tid + r), 10 (4 tid + r)
     {
@@ -196,7 +235,28 @@ __device__ __forceinline__ void tile4096_dev(const TileJob &J, uint32_t N, uint3
 #pragma unroll
         for (int r = 0; r < 4; ++r) tc[3 + r] = twiddle_from(J.U[1024 + 4 * tid + r], e10[0], e10[1], e10[2], p);
     }
-    fwd2<4, 3>(a, x, [&](int d, int j) { return tc[(1 << d) - 1 + j]; }, p, p2);
+    auto twC = [&](int d, int j) { return tc[(1 << d) - 1 + j]; };
+    if (DO_A && DO_X)
+        fwd2<4, 3>(a, x, twC, p, p2);
+    else if (DO_A)
+        fwd1<4, 3, false>(a, twC, p, p2);
+    else
+        fwd1<4, 3, true>(x, twC, p, p2);
+    if constexpr (VAR == TILE_ROW) {
+        // the transformed row vector, 16 contiguous residues per thread
+        uint4 *d = reinterpret_cast<uint4 *>(J.dst + base + 16 * tid);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) d[q] = make_uint4(a[4 * q], a[4 * q + 1], a[4 * q + 2], a[4 * q + 3]);
+        return;
+    }
+    if constexpr (VAR == TILE_PLANNED) {
+        const uint4 *s = reinterpret_cast<const uint4 *>(static_cast<const uint32_t *>(J.a.ptr) + base + 16 * tid);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const uint4 va = __ldg(s + q);
+            a[4 * q] = va.x; a[4 * q + 1] = va.y; a[4 * q + 2] = va.z; a[4 * q + 3] = va.w;
+        }
+    }
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
         Tw phi = tc[3 + (q >> 1)];
