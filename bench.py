@@ -299,9 +299,10 @@ def _time(fn, reps, flush, stream, warm=2):
 
 def run_extras(F, I, dev, stream):
     """The other workloads of the method, each on its own inputs: single
-    products, the complex layer's fused forward+backward against the plain
-    three-product method, the batched launch against per-instance calls, and
-    the large-integer product.  Times in ms (median, min)."""
+    products, products with a fixed-matrix plan against plain ones, the
+    complex layer's fused forward+backward against the plain three-product
+    method, the batched launch against per-instance calls, and the
+    large-integer product.  Times in ms (median, min)."""
     import numpy as np
     import torch
     out = {}
@@ -315,6 +316,24 @@ def run_extras(F, I, dev, stream):
         dc = torch.empty_like(da)
         med, mn = _time(lambda: F.fcirc_matvec(I.P1, 1, da, dx, out=dc, stream=stream), 20, flush, stream)
         out[f"fcirc_matvec_n2^{m}"] = {"ms": med, "ms_min": mn, "Gelem_s": n / (med * 1e-3) / 1e9}
+    # fixed-matrix plan: the same A for many vectors (the row vector's tree
+    # once, two trees per product) against the plain product, n = 2^24
+    n = 1 << 24
+    a, x = I.single_mod(n, seed=I.SEED_BASE + 10)
+    da = torch.from_numpy(a.view(np.int32)).to(dev)
+    dx = torch.from_numpy(x.view(np.int32)).to(dev)
+    dc = torch.empty_like(da)
+    dc2 = torch.empty_like(da)
+    with F.APlan(I.P1, 1, da, stream=stream) as plan:
+        pm_, pmin_ = _time(lambda: plan.matvec(dx, out=dc2, stream=stream), 20, flush, stream)
+        F.fcirc_matvec(I.P1, 1, da, dx, out=dc, stream=stream)
+        torch.cuda.synchronize()
+        assert torch.equal(dc, dc2), "planned product differs from the plain one"
+    tm, tmin = _time(lambda: F.fcirc_matvec_t(I.P1, 1, da, dx, out=dc, stream=stream), 20, flush, stream)
+    out["fcirc_matvec_t_n2^24"] = {"ms": tm, "ms_min": tmin, "Gelem_s": n / (tm * 1e-3) / 1e9}
+    plain = out["fcirc_matvec_n2^24"]["ms"]
+    out["fcirc_matvec_aplan_n2^24"] = {"ms": pm_, "ms_min": pmin_, "Gelem_s": n / (pm_ * 1e-3) / 1e9,
+                                       "speedup_vs_plain": plain / pm_}
     # complex layer: fused forward + backward vs forward and two plain products
     batch, n = 4096, 1024
     a, x, g = I.complex_layer(batch, n)

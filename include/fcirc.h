@@ -78,6 +78,21 @@ int fcirc_matvec(uint32_t p, uint32_t f, const uint32_t *a, const uint32_t *x,
                  uint32_t *c, uint64_t n, void *stream);
 
 /*
+ * fcirc_matvec_t -- c = A^T x for the same f-circulant A (row vector a):
+ * the column convention, c[j] = sum_i A[i][j] x[i], which is the product
+ * a(z) x(z) mod (z^n - f) of the two vectors read as polynomials (Section
+ * 1.2 relates the two conventions; Section 3.1 uses this one).  Arguments,
+ * memory, errors and synchronisation as for fcirc_matvec.
+ *
+ * It runs the row-convention product of Algorithm 1 with parameter f^-1 on
+ * the reversed row vector (a[n-1-k], read reversed by the first pass, no
+ * copy) and stores that result rotated by one and scaled by f:
+ * c[n-1] = c'[0], c[j] = f c'[j+1].
+ */
+int fcirc_matvec_t(uint32_t p, uint32_t f, const uint32_t *a, const uint32_t *x,
+                   uint32_t *c, uint64_t n, void *stream);
+
+/*
  * fcirc_matvec_noalloc -- the same product as fcirc_matvec for callers that
  * cannot let the library allocate device memory (a process that reserved
  * its GPU memory in fixed pools up front, or that must not see the

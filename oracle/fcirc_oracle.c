@@ -91,6 +91,25 @@ void oracle_fcirc_matvec_mod_rows(uint32_t p, uint32_t f, const uint32_t *a,
         out[k] = (uint32_t)fcirc_row_mod(p, f, a, x, n, rows[k]);
 }
 
+/* Column convention: c[j] = sum_i A[i][j] x[i], which is coefficient j of
+ * a(z) x(z) reduced modulo z^n - f: the terms a[m] x[t] with m + t = j
+ * count once, those with m + t = j + n count f times (Section 1.2 relates
+ * the row and column conventions). */
+void oracle_fcirc_matvec_t_mod(uint32_t p, uint32_t f, const uint32_t *a,
+                               const uint32_t *x, uint32_t *c, uint64_t n)
+{
+    #pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t jj = 0; jj < (int64_t)n; ++jj) {
+        const uint64_t j = (uint64_t)jj;
+        uint64_t direct = 0, wrapped = 0;
+        for (uint64_t m = 0; m <= j; ++m)
+            direct = (direct + mulmod_u64(a[m], x[j - m], p)) % p;
+        for (uint64_t m = j + 1; m < n; ++m)
+            wrapped = (wrapped + mulmod_u64(a[m], x[j + n - m], p)) % p;
+        c[j] = (uint32_t)((direct + mulmod_u64(f % p, wrapped, p)) % p);
+    }
+}
+
 /* A batch of independent products with per-instance f and length
  * n_i = offsets[i+1] - offsets[i]; a, x, c are packed back to back. */
 void oracle_fcirc_matvec_mod_batched(uint32_t p, const uint32_t *f,

@@ -55,6 +55,7 @@ def lib():
             L.oracle_num_threads.restype = ctypes.c_int
             L.oracle_fcirc_matvec_mod.argtypes = [U32, U32, u32p, u32p, u32p, U64]
             L.oracle_fcirc_matvec_mod_rows.argtypes = [U32, U32, u32p, u32p, U64, u64p, U64, u32p]
+            L.oracle_fcirc_matvec_t_mod.argtypes = [U32, U32, u32p, u32p, u32p, U64]
             L.oracle_fcirc_matvec_mod_batched.argtypes = [U32, u32p, u64p, u32p, u32p, u32p, U32]
             L.oracle_fcirc_matvec_c128.argtypes = [F64, F64, f64p, f64p, f64p, U64, U64]
             L.oracle_fcirc_grad_c128.argtypes = [F64, F64, f64p, f64p, f64p, f64p, f64p, U64, U64]
@@ -89,6 +90,15 @@ def fcirc_matvec_mod(p: int, f: int, a, x) -> np.ndarray:
     assert a.shape == x.shape and a.ndim == 1
     c = np.empty_like(a)
     lib().oracle_fcirc_matvec_mod(p, f % p, a, x, c, a.size)
+    return c
+
+
+def fcirc_matvec_t_mod(p: int, f: int, a, x) -> np.ndarray:
+    """A^T x (column convention): a(z) x(z) mod (z^n - f), schoolbook."""
+    a, x = _u32(a), _u32(x)
+    assert a.shape == x.shape and a.ndim == 1
+    c = np.empty_like(a)
+    lib().oracle_fcirc_matvec_t_mod(p, f % p, a, x, c, a.size)
     return c
 
 

@@ -26,7 +26,7 @@ from . import build as _build
 
 __all__ = [
     "FcircError", "library_path", "load",
-    "fcirc_matvec", "fcirc_matvec_noalloc", "APlan", "poly_mul_int", "bigint_mul",
+    "fcirc_matvec", "fcirc_matvec_t", "fcirc_matvec_noalloc", "APlan", "poly_mul_int", "bigint_mul",
     "fcirc_matvec_c64", "fcirc_matvec_backward", "fcirc_layer",
     "fcirc_matvec_batched", "batched_autotune", "BatchedGraph", "sync_status", "release",
     "nth_root", "node_twiddle", "leaf_param", "twiddle_from_factor",
@@ -45,6 +45,7 @@ _vp = ctypes.c_void_p
 _SIGNATURES = {
     "fcirc_matvec": ([_u32, _u32, _vp, _vp, _vp, _u64, _vp], _i32),
     "fcirc_matvec_noalloc": ([_u32, _u32, _vp, _vp, _vp, _u64, _vp], _i32),
+    "fcirc_matvec_t": ([_u32, _u32, _vp, _vp, _vp, _u64, _vp], _i32),
     "fcirc_aplan_create": ([_u32, _u32, _vp, _u64, _vp, ctypes.POINTER(_vp)], _i32),
     "fcirc_matvec_aplan": ([_vp, _vp, _vp, _vp], _i32),
     "fcirc_aplan_destroy": ([_vp], _i32),
@@ -146,6 +147,24 @@ def fcirc_matvec(p: int, f: int, a, x, out=None, stream=None):
     st = _stream_handle(stream, a, x, out)
     _check(load().fcirc_matvec(p, f % p, a.data_ptr(), x.data_ptr(), out.data_ptr(), a.numel(), st),
            "fcirc_matvec")
+    return out
+
+
+def fcirc_matvec_t(p: int, f: int, a, x, out=None, stream=None):
+    """c = A^T x for the f-circulant A with row vector a (include/fcirc.h):
+    the column convention, a(z) x(z) mod (z^n - f).  Same arguments as
+    fcirc_matvec."""
+    import torch
+    _u32_tensor(a, "a")
+    _u32_tensor(x, "x")
+    if a.shape != x.shape or a.dim() != 1:
+        raise ValueError("a and x must be 1-D of the same length")
+    if out is None:
+        out = torch.empty_like(a)
+    _u32_tensor(out, "out")
+    st = _stream_handle(stream, a, x, out)
+    _check(load().fcirc_matvec_t(p, f % p, a.data_ptr(), x.data_ptr(), out.data_ptr(), a.numel(), st),
+           "fcirc_matvec_t")
     return out
 
 

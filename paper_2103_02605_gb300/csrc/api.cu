@@ -247,6 +247,41 @@ Src src_u32(const void *ptr, uint64_t n) { return Src{ptr, n, SRC_U32, 0, Tw{0, 
 
 }  // namespace
 
+// The f-circulant product c = A x for n >= 2 with the plan pl: row vector
+// source sa (scaled by 2^32 2^-L on its first load), vector source sx, the
+// row side worked in c itself, the vector side in xs (n words, used when the
+// column passes run).  Canonical output.
+static int matvec_core(const Plan *pl, const Src &sa, const Src &sx, uint32_t *dc, uint32_t *xs, cudaStream_t s)
+{
+    const uint64_t n = pl->n;
+    if (pl->k == 0) {
+        TileParams tp;
+        tp.job[0] = tile_job(pl, sa, sx, dc, 0);
+        tp.N = n;
+        tp.logT = pl->logT;
+        tp.D = pl->D;
+        return run_tile(tp, 1, 1, s);
+    }
+    for (int i = 0; i < pl->npass; ++i) {
+        FwdDesc jd[2] = {FwdDesc{i == 0 ? sa : src_u32(dc, n), dc, pl, 0, 0},
+                         FwdDesc{i == 0 ? sx : src_u32(xs, n), xs, pl, 1, 0}};
+        FCIRC_TRY(run_fwd_pass(i, jd, 2, 1, s));
+    }
+    {
+        TileParams tp;
+        tp.job[0] = tile_job(pl, src_u32(dc, n), src_u32(xs, n), dc, 1);
+        tp.N = n;
+        tp.logT = pl->logT;
+        tp.D = pl->D;
+        FCIRC_TRY(run_tile(tp, (uint64_t)1 << pl->k, 1, s));
+    }
+    for (int i = pl->npass - 1; i >= 0; --i) {
+        InvDesc jd[1] = {InvDesc{dc, dc, pl}};
+        FCIRC_TRY(run_inv_pass(i, jd, 1, i == 0 ? EPI_CANON : EPI_LAZY, nullptr, 0, nullptr, s));
+    }
+    return FCIRC_OK;
+}
+
 // The three NTT-friendly primes of the polynomial and large-integer
 // products (2^23, 2^26 and 2^25 divide p - 1; their product exceeds 2^85).
 static const uint32_t kPrimes[3] = {998244353u, 469762049u, 167772161u};
@@ -364,34 +399,42 @@ int fcirc_matvec(uint32_t p, uint32_t f, const uint32_t *a, const uint32_t *x, u
         return st.end();
     }
     // the row vector is scaled by 2^32 2^-L on its first load (see leaf2)
-    const Src sa{da, n, SRC_U32, 1, pl->kt}, sx = src_u32(dx, n);
-    if (pl->k == 0) {
-        TileParams tp;
-        tp.job[0] = tile_job(pl, sa, sx, dc, 0);
-        tp.N = n;
-        tp.logT = pl->logT;
-        tp.D = pl->D;
-        FCIRC_TRY(run_tile(tp, 1, 1, s));
+    const Src sa{da, n, SRC_U32, 1, pl->kt};
+    FCIRC_TRY(matvec_core(pl, sa, src_u32(dx, n), dc, reinterpret_cast<uint32_t *>(st.scratch), s));
+    return st.end();
+}
+
+int fcirc_matvec_t(uint32_t p, uint32_t f, const uint32_t *a, const uint32_t *x, uint32_t *c, uint64_t n,
+                   void *stream)
+{
+    set_error("");
+    if (!a || !x || !c) return fail(FCIRC_EINVAL, "fcirc_matvec_t: null pointer");
+    if (!is_pow2(n)) return fail(FCIRC_EINVAL, "fcirc_matvec_t: n = %llu is not a power of two",
+                                 (unsigned long long)n);
+    if (n > ((uint64_t)1 << kMaxLogN)) return fail(FCIRC_EINVAL, "fcirc_matvec_t: n above 2^%d", kMaxLogN);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const PrimeTables *pt;
+    FCIRC_TRY(prime_tables(p, &pt));
+    if (f % p == 0) return fail(FCIRC_ENOROOT, "f = 0 has no inverse (Theorem 1)");
+    // A^T x = the row product with parameter f^-1 of the reversed row vector,
+    // rotated by one and scaled by f (all but its first element)
+    const uint32_t fi = host::invmod(f % p, p);
+    const Plan *pl = nullptr;
+    if (n > 1) FCIRC_TRY(get_plan(p, fi, n, &pl));
+    Arg aa{a, n * 4, true, false}, ax{x, n * 4, true, false}, ac{c, n * 4, false, true};
+    Staging st;
+    st.args = {&aa, &ax, &ac};
+    FCIRC_TRY(st.begin(s, 2 * n * 4));
+    const uint32_t *da = static_cast<const uint32_t *>(aa.d), *dx = static_cast<const uint32_t *>(ax.d);
+    uint32_t *dc = static_cast<uint32_t *>(ac.d);
+    if (n == 1) {
+        FCIRC_TRY(launch_scalar(da, dx, dc, p, s));
         return st.end();
     }
-    uint32_t *xs = reinterpret_cast<uint32_t *>(st.scratch);
-    for (int i = 0; i < pl->npass; ++i) {
-        FwdDesc jd[2] = {FwdDesc{i == 0 ? sa : src_u32(dc, n), dc, pl, 0, 0},
-                         FwdDesc{i == 0 ? sx : src_u32(xs, n), xs, pl, 1, 0}};
-        FCIRC_TRY(run_fwd_pass(i, jd, 2, 1, s));
-    }
-    {
-        TileParams tp;
-        tp.job[0] = tile_job(pl, src_u32(dc, n), src_u32(xs, n), dc, 1);
-        tp.N = n;
-        tp.logT = pl->logT;
-        tp.D = pl->D;
-        FCIRC_TRY(run_tile(tp, (uint64_t)1 << pl->k, 1, s));
-    }
-    for (int i = pl->npass - 1; i >= 0; --i) {
-        InvDesc jd[1] = {InvDesc{dc, dc, pl}};
-        FCIRC_TRY(run_inv_pass(i, jd, 1, i == 0 ? EPI_CANON : EPI_LAZY, nullptr, 0, nullptr, s));
-    }
+    uint32_t *cr = reinterpret_cast<uint32_t *>(st.scratch), *xs = cr + n;
+    const Src sa{da, n, SRC_U32_REV, 1, pl->kt};
+    FCIRC_TRY(matvec_core(pl, sa, src_u32(dx, n), cr, xs, s));
+    FCIRC_TRY(launch_rot_scale(cr, dc, n, Tw{f % p, host::shoup_quot(f % p, p)}, p, s));
     return st.end();
 }
 

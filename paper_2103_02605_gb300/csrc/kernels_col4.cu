@@ -189,6 +189,10 @@ __device__ __forceinline__ uint4 ld4_raw(const Src &s, uint32_t N, uint32_t idx)
     constexpr int KIND = MODE & 3;
     if constexpr (KIND == SRC_U32) {
         return __ldg(reinterpret_cast<const uint4 *>(static_cast<const uint32_t *>(s.ptr) + idx));
+    } else if constexpr (KIND == SRC_U32_REV) {
+        // a'[idx + c] = a[N - 1 - idx - c]: the word N - 4 - idx + (3 - c)
+        const uint4 w = __ldg(reinterpret_cast<const uint4 *>(static_cast<const uint32_t *>(s.ptr) + N - 4 - idx));
+        return make_uint4(w.w, w.z, w.y, w.x);
     } else if constexpr (KIND == SRC_U16_REV) {
         // a'[idx + c] = P[N - 1 - idx - c]: P[j0 + 3 - c] with j0 = N - 4 - idx
         const uint16_t *q = static_cast<const uint16_t *>(s.ptr);
@@ -639,7 +643,7 @@ bool aligned(const void *ptr, unsigned a) { return (reinterpret_cast<uintptr_t>(
 
 bool src_aligned(const Src &s)
 {
-    return s.kind == SRC_U32 ? aligned(s.ptr, 16) : aligned(s.ptr, 8);
+    return (s.kind == SRC_U32 || s.kind == SRC_U32_REV) ? aligned(s.ptr, 16) : aligned(s.ptr, 8);
 }
 
 template <int LF, int M0, int M1>
@@ -669,6 +673,7 @@ template <int LF>
 int launch_c4fwd_lf(const ColFwdParams &P, int nctay, int m0, int m1, cudaStream_t s)
 {
     if (m0 == MODE_U32_S && m1 == MODE_U32) return launch_c4fwd_m<LF, MODE_U32_S, MODE_U32>(P, nctay, s);
+    if (m0 == MODE_U32REV_S && m1 == MODE_U32) return launch_c4fwd_m<LF, MODE_U32REV_S, MODE_U32>(P, nctay, s);
     if (m0 == MODE_U32 && m1 == MODE_U32) return launch_c4fwd_m<LF, MODE_U32, MODE_U32>(P, nctay, s);
     if (m0 == MODE_REV_S_H && m1 == MODE_U16_H) return launch_c4fwd_m<LF, MODE_REV_S_H, MODE_U16_H>(P, nctay, s);
     if (m0 == MODE_REV_S && m1 == MODE_U16) return launch_c4fwd_m<LF, MODE_REV_S, MODE_U16>(P, nctay, s);

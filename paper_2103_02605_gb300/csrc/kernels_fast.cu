@@ -393,6 +393,7 @@ static int launch_colfwd_lf(const ColFwdParams &P, int nctay, cudaStream_t s)
                 return fail(FCIRC_EINVAL, "column pass: mixed source modes in one job group");
         }
     if (m0 == MODE_U32_S && m1 == MODE_U32) return launch_colfwd_m<LF, MODE_U32_S, MODE_U32>(P, nctay, s);
+    if (m0 == MODE_U32REV_S && m1 == MODE_U32) return launch_colfwd_m<LF, MODE_U32REV_S, MODE_U32>(P, nctay, s);
     if (m0 == MODE_U32 && m1 == MODE_U32) return launch_colfwd_m<LF, MODE_U32, MODE_U32>(P, nctay, s);
     if (m0 == MODE_REV_S_H && m1 == MODE_U16_H) return launch_colfwd_m<LF, MODE_REV_S_H, MODE_U16_H>(P, nctay, s);
     if (m0 == MODE_REV_S && m1 == MODE_U16) return launch_colfwd_m<LF, MODE_REV_S, MODE_U16>(P, nctay, s);

@@ -243,6 +243,24 @@ int launch_crt_rot(const uint32_t *r1, const uint32_t *r2, const uint32_t *r3, u
     return FCIRC_OK;
 }
 
+// Transposed product from the row product of the reversed row vector with
+// parameter f^-1: d[n-1] = c'[0], d[j] = f c'[j+1] (canonical in and out).
+__global__ void k_rot_scale(const uint32_t *src, uint32_t *dst, uint64_t n, Tw f, uint32_t p)
+{
+    for (uint64_t j = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; j < n; j += (uint64_t)gridDim.x * blockDim.x)
+        dst[j] = j + 1 < n ? reduce_once(shoup_mul(src[j + 1], f.w, f.wp, p), p) : src[0];
+}
+
+int launch_rot_scale(const uint32_t *src, uint32_t *dst, uint64_t n, Tw f, uint32_t p, cudaStream_t s)
+{
+    unsigned blocks = (unsigned)((n + 255) / 256);
+    if (blocks > 152 * 8) blocks = 152 * 8;
+    ProfScope ps("k_rot_scale", s);
+    k_rot_scale<<<blocks, 256, 0, s>>>(src, dst, n, f, p);
+    FCIRC_CUDA_TRY(cudaGetLastError());
+    return FCIRC_OK;
+}
+
 int launch_scalar(const uint32_t *a, const uint32_t *x, uint32_t *c, uint32_t p, cudaStream_t s)
 {
     ProfScope ps("k_scalar", s);

@@ -11,7 +11,7 @@ constexpr int kTileThreads = 256;
 constexpr int kStrThreads = 256;
 constexpr int kStrSmemMax = 200 * 1024;
 
-enum SrcKind { SRC_U32 = 0, SRC_U16_REV = 1, SRC_U16 = 2 };
+enum SrcKind { SRC_U32 = 0, SRC_U16_REV = 1, SRC_U16 = 2, SRC_U32_REV = 3 };
 
 // Where a pass reads its input: a uint32 array (residues), or 16-bit
 // coefficients zero-padded to the transform length, optionally reversed
@@ -156,6 +156,7 @@ struct ColInvParams {
 int launch_tile(const TileParams &P, uint64_t ntiles, int njobs, cudaStream_t s);
 int launch_strided_fwd(const StrFwdParams &P, int njobs, cudaStream_t s);
 int launch_strided_inv(const StrInvParams &P, cudaStream_t s);
+int launch_rot_scale(const uint32_t *src, uint32_t *dst, uint64_t n, Tw f, uint32_t p, cudaStream_t s);
 int launch_crt_rot(const uint32_t *r1, const uint32_t *r2, const uint32_t *r3, uint64_t N,
                    uint64_t *out, uint64_t nout, const CrtConsts &C, cudaStream_t s);
 // register-staged kernels (kernels_fast.cu) for the shapes they cover

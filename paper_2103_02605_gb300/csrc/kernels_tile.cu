@@ -71,6 +71,8 @@ int launch_tile_fast(const TileParams &P, uint64_t ntiles, int njobs, cudaStream
         k_tile4096<MODE_U32, MODE_U32><<<grid, 256, 0, s>>>(P);
     else if (ma == MODE_U32_S && mx == MODE_U32)
         k_tile4096<MODE_U32_S, MODE_U32><<<grid, 256, 0, s>>>(P);
+    else if (ma == MODE_U32REV_S && mx == MODE_U32)
+        k_tile4096<MODE_U32REV_S, MODE_U32><<<grid, 256, 0, s>>>(P);
     else if (ma == MODE_REV_S && mx == MODE_U16)
         k_tile4096<MODE_REV_S, MODE_U16><<<grid, 256, 0, s>>>(P);
     else

@@ -24,6 +24,10 @@ __device__ __forceinline__ uint32_t load_src(const Src &s, uint64_t N, uint64_t 
         v = j < s.len ? static_cast<const uint16_t *>(s.ptr)[j] : 0u;
         break;
     }
+    case SRC_U32_REV:
+        // a'[idx] = a[N-1-idx]
+        v = static_cast<const uint32_t *>(s.ptr)[N - 1 - idx];
+        break;
     default:  // SRC_U16
         v = idx < s.len ? static_cast<const uint16_t *>(s.ptr)[idx] : 0u;
     }
@@ -39,6 +43,7 @@ enum : int {
     MODE_U32 = SRC_U32,
     MODE_U32_S = SRC_U32 | 4,
     MODE_REV_S = SRC_U16_REV | 4,
+    MODE_U32REV_S = SRC_U32_REV | 4,
     MODE_REV_S_H = SRC_U16_REV | 4 | (1 << 3),
     MODE_U16 = SRC_U16,
     MODE_U16_H = SRC_U16 | (2 << 3),
@@ -50,6 +55,8 @@ __device__ __forceinline__ uint32_t ld_raw(const Src &s, uint32_t N, uint32_t id
     constexpr int KIND = MODE & 3;
     if constexpr (KIND == SRC_U32) {
         return static_cast<const uint32_t *>(s.ptr)[idx];
+    } else if constexpr (KIND == SRC_U32_REV) {
+        return static_cast<const uint32_t *>(s.ptr)[N - 1 - idx];   // a'[idx] = a[N-1-idx]
     } else if constexpr (KIND == SRC_U16_REV) {
         const uint32_t j = N - 1 - idx;   // a'[idx] = P[N-1-idx], P zero-padded
         return j < s.len ? (uint32_t) static_cast<const uint16_t *>(s.ptr)[j] : 0u;

@@ -124,6 +124,68 @@ def test_matvec_unaligned_views_take_the_one_column_kernels(F, orc, m):
     assert np.array_equal(got[rows.astype(np.int64)], orc.fcirc_matvec_mod_rows(P2, f, a, x, rows))
 
 
+@pytest.mark.parametrize("m", [0, 1, 2, 5, 12, 13])
+def test_matvec_transposed_vs_oracle(F, orc, m):
+    """fcirc_matvec_t (column convention, A^T x) against the oracle's
+    a(z) x(z) mod (z^n - f)."""
+    import torch
+    n = 1 << m
+    for p in (P1, P3):
+        g = I.SplitMix64(900 + m + p % 97)
+        a, x = g.uniform_mod(p, n), g.uniform_mod(p, n)
+        for f in (1, p - 1, f_with_root(p, n, 3 * m + 1)):
+            if n > 2 and f == p - 1 and pow(p - 1, (p - 1) // int(np.gcd(n // 2, p - 1)), p) != 1:
+                continue
+            c = F.fcirc_matvec_t(p, f, dev_u32(a), dev_u32(x))
+            torch.cuda.synchronize()
+            assert np.array_equal(host_u32(c), orc.fcirc_matvec_t_mod(p, f, a, x)), (p, m, f)
+
+
+def _powers_mod(t, n, p):
+    """t^k mod p for k < n (n a power of two), in blocks of 4096."""
+    lo = np.empty(min(n, 4096), np.uint64)
+    acc = 1
+    for k in range(lo.size):
+        lo[k] = acc
+        acc = acc * t % p
+    if n <= 4096:
+        return lo
+    step = pow(t, 4096, p)
+    hi = np.empty(n // 4096, np.uint64)
+    acc = 1
+    for k in range(hi.size):
+        hi[k] = acc
+        acc = acc * step % p
+    return ((hi[:, None] * lo[None, :]) % p).reshape(-1)
+
+
+def _eval_mod(coef, pw, p):
+    # each product is below 2^60 and reduced before the sum (below 2^54)
+    return int(((coef.astype(np.uint64) * pw) % p).sum(dtype=np.uint64) % p)
+
+
+@pytest.mark.parametrize("m", [20, 24])
+def test_matvec_transposed_large_by_evaluation(F, m):
+    """A^T x = a(z) x(z) mod (z^n - f): at any root t of z^n - f the values
+    satisfy c(t) = a(t) x(t) mod p.  Two roots t = r w^k with f = r^n."""
+    import torch
+    n, p = 1 << m, P1
+    g = I.SplitMix64(950 + m)
+    a, x = g.uniform_mod(p, n), g.uniform_mod(p, n)
+    r = 123457
+    f = pow(r, n, p)
+    c = host_u32(F.fcirc_matvec_t(p, f, dev_u32(a), dev_u32(x)))
+    torch.cuda.synchronize()
+    w = I.primitive_2k_root(p, min(m, 23))   # w^n = 1
+    for k in (1, 12345):
+        t = r * pow(w, k, p) % p
+        assert pow(t, n, p) == f
+        pw = _powers_mod(t, n, p)
+        ca = _eval_mod(a, pw, p)
+        cx = _eval_mod(x, pw, p)
+        assert _eval_mod(c, pw, p) == ca * cx % p
+
+
 def test_matvec_config0_full(F, orc):
     """n = 2^12, f = 1, p = 998244353: the single-instance workload, full vector."""
     a, x = I.single_mod(1 << 12)

@@ -36,6 +36,12 @@ MUTANTS = {
     # gradient of x with A instead of A^H
     "grad_x_no_conj": ("sx += conj(fcirc_entry_c(f, ab, n, i, (uint64_t)k)) * ld(gb, i);",
                        "sx += fcirc_entry_c(f, ab, n, i, (uint64_t)k) * ld(gb, i);"),
+    # column convention: f missing from the wrapped terms
+    "t_drop_f": ("c[j] = (uint32_t)((direct + mulmod_u64(f % p, wrapped, p)) % p);",
+                 "c[j] = (uint32_t)((direct + wrapped) % p);"),
+    # column convention: wrapped terms indexed without the wrap
+    "t_wrong_wrap": ("wrapped = (wrapped + mulmod_u64(a[m], x[j + n - m], p)) % p;",
+                     "wrapped = (wrapped + mulmod_u64(a[m], x[m - j - 1], p)) % p;"),
     # off-by-one in the polynomial product window
     "poly_window": ("for (uint64_t i = lo; i <= hi; ++i)\n        s +=",
                     "for (uint64_t i = lo + 1; i <= hi; ++i)\n        s +="),
@@ -54,6 +60,7 @@ PIN_CALLS = [
     lambda o: pins.test_f1_is_ordinary_circulant_fft(o, 32),
     lambda o: pins.test_general_f_by_diagonal_scaling_fft(o, 8, 2.0),
     lambda o: pins.test_transpose_is_polynomial_product_mod_xn_minus_f(o, 8),
+    lambda o: pins.test_column_convention_is_the_transpose(o, 8),
     lambda o: pins.test_algorithm1_bruteforce_equals_dense(o, 16, None),
     lambda o: pins.test_complex_gradients_finite_differences(o, 0.6 + 0.8j),
     lambda o: pins.test_complex_gradients_finite_differences(o, 2.0 - 0.5j),

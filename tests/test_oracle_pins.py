@@ -194,6 +194,28 @@ def test_transpose_is_polynomial_product_mod_xn_minus_f(orc, n):
     assert atx == red
 
 
+@pytest.mark.parametrize("n", [1, 2, 3, 5, 8, 16])
+def test_column_convention_is_the_transpose(orc, n):
+    """The column-convention oracle equals A^T x with A built column by
+    column from the row-convention oracle (A e_j), and reduces to the
+    identity for a = e_0 and to a for x = e_0."""
+    rng = np.random.default_rng(400 + n)
+    a = rand_mod(rng, n)
+    x = rand_mod(rng, n)
+    f = int(rng.integers(1, P))
+    cols = []
+    for j in range(n):
+        e = np.zeros(n, np.uint32)
+        e[j] = 1
+        cols.append([int(v) for v in orc.fcirc_matvec_mod(P, f, a, e)])
+    want = [sum(cols[j][i] * int(x[i]) for i in range(n)) % P for j in range(n)]
+    assert [int(v) for v in orc.fcirc_matvec_t_mod(P, f, a, x)] == want
+    e0 = np.zeros(n, np.uint32)
+    e0[0] = 1
+    assert np.array_equal(orc.fcirc_matvec_t_mod(P, f, e0, x), x)
+    assert np.array_equal(orc.fcirc_matvec_t_mod(P, f, a, e0), a)
+
+
 # -- the paper's Algorithm 1 (brute force) agrees with the dense oracle ----------
 
 @pytest.mark.parametrize("n", [1, 2, 4, 8, 16, 32])
