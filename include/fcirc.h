@@ -65,17 +65,42 @@ enum fcirc_status {
  *   f     the circulant parameter, 1 <= f < p (f = 1: ordinary circulant).
  *   a, x  n residues each, in [0, p) (row vector and vector).
  *   c     n residues out, canonical in [0, p).
- *   n     a power of two, 1 <= n <= 2^(v+1) where 2^v is the largest power
- *         of two dividing p-1 (the recursion halves down to 2x2 blocks, so
- *         it needs 2^(log2 n - 1)-th roots of unity), and n <= 2^28.
+ *   n     1 <= n.  A power of two runs Algorithm 1 directly: then
+ *         n <= 2^(v+1) where 2^v is the largest power of two dividing p-1
+ *         (the recursion halves down to 2x2 blocks, so it needs
+ *         2^(log2 n - 1)-th roots of unity), and n <= 2^28.  Any other n
+ *         goes through Corollary 1 (below).
  *
- * Errors: FCIRC_EINVAL for a null pointer, n = 0, n not a power of two or
- * too large, or p out of range / not prime; FCIRC_ENOROOT when f = 0 or f
+ * Errors: FCIRC_EINVAL for a null pointer, n = 0 or too large, or p out of
+ * range / not prime; FCIRC_ENOROOT when n is a power of two and f = 0 or f
  * has no (n/2)-th root mod p (Theorem 1 needs a root of f at every level).
  * Results for entries outside [0, p) are unspecified (never out of bounds).
  */
 int fcirc_matvec(uint32_t p, uint32_t f, const uint32_t *a, const uint32_t *x,
                  uint32_t *c, uint64_t n, void *stream);
+
+/*
+ * (fcirc_matvec, continued) n that is not a power of two (Corollary 1):
+ * the product is the first n entries of an ordinary circulant (f = 1)
+ * product of size N, the power of two with N >= 2n - 1, whose row vector is
+ * a[0..n) | zeros | f a[1..n) and whose vector is x | zeros (the corollary
+ * takes N = 2^(d+1) with 2^d > n; any N >= 2n - 1 leaves the gap it needs).
+ * It needs only the roots of unity of N and no root of f, so every
+ * 0 <= f < p is accepted; n is limited by N <= 2^28 and by the 2-adic
+ * order of p - 1 (FCIRC_ENOROOT).  Scratch: 16 N bytes.
+ */
+
+/*
+ * fcirc_toeplitz_matvec -- c = T x over Z/pZ for the n x n Toeplitz matrix
+ * T[i][j] = t[j - i + n - 1] (t holds the 2n - 1 diagonals, from the lowest
+ * t[0] = T[n-1][0] to the highest t[2n-2] = T[0][n-1]), any n >= 1.  The
+ * paper's introduction recalls that Toeplitz products reduce to circulant
+ * ones; this is Corollary 1's embedding with the wrapped part of the row
+ * vector taken from the lower diagonals.  Memory, errors and
+ * synchronisation as for fcirc_matvec.
+ */
+int fcirc_toeplitz_matvec(uint32_t p, const uint32_t *t, const uint32_t *x, uint32_t *c, uint64_t n,
+                          void *stream);
 
 /*
  * fcirc_matvec_t -- c = A^T x for the same f-circulant A (row vector a):

@@ -110,6 +110,20 @@ void oracle_fcirc_matvec_t_mod(uint32_t p, uint32_t f, const uint32_t *a,
     }
 }
 
+/* Toeplitz product c = T x, T[i][j] = t[j - i + n - 1] (t: the 2n - 1
+ * diagonals, lowest first), straight from the definition. */
+void oracle_toeplitz_matvec_mod(uint32_t p, const uint32_t *t, const uint32_t *x, uint32_t *c, uint64_t n)
+{
+    #pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t ii = 0; ii < (int64_t)n; ++ii) {
+        const uint64_t i = (uint64_t)ii;
+        uint64_t acc = 0;
+        for (uint64_t j = 0; j < n; ++j)
+            acc = (acc + mulmod_u64(t[j + n - 1 - i], x[j], p)) % p;
+        c[i] = (uint32_t)acc;
+    }
+}
+
 /* A batch of independent products with per-instance f and length
  * n_i = offsets[i+1] - offsets[i]; a, x, c are packed back to back. */
 void oracle_fcirc_matvec_mod_batched(uint32_t p, const uint32_t *f,

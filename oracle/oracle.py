@@ -56,6 +56,7 @@ def lib():
             L.oracle_fcirc_matvec_mod.argtypes = [U32, U32, u32p, u32p, u32p, U64]
             L.oracle_fcirc_matvec_mod_rows.argtypes = [U32, U32, u32p, u32p, U64, u64p, U64, u32p]
             L.oracle_fcirc_matvec_t_mod.argtypes = [U32, U32, u32p, u32p, u32p, U64]
+            L.oracle_toeplitz_matvec_mod.argtypes = [U32, u32p, u32p, u32p, U64]
             L.oracle_fcirc_matvec_mod_batched.argtypes = [U32, u32p, u64p, u32p, u32p, u32p, U32]
             L.oracle_fcirc_matvec_c128.argtypes = [F64, F64, f64p, f64p, f64p, U64, U64]
             L.oracle_fcirc_grad_c128.argtypes = [F64, F64, f64p, f64p, f64p, f64p, f64p, U64, U64]
@@ -99,6 +100,15 @@ def fcirc_matvec_t_mod(p: int, f: int, a, x) -> np.ndarray:
     assert a.shape == x.shape and a.ndim == 1
     c = np.empty_like(a)
     lib().oracle_fcirc_matvec_t_mod(p, f % p, a, x, c, a.size)
+    return c
+
+
+def toeplitz_matvec_mod(p: int, t, x) -> np.ndarray:
+    """T x for T[i][j] = t[j - i + n - 1] (t: 2n - 1 diagonals), dense."""
+    t, x = _u32(t), _u32(x)
+    assert x.ndim == 1 and t.shape == (2 * x.size - 1,)
+    c = np.empty_like(x)
+    lib().oracle_toeplitz_matvec_mod(p, t, x, c, x.size)
     return c
 
 

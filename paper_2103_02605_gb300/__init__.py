@@ -26,7 +26,7 @@ from . import build as _build
 
 __all__ = [
     "FcircError", "library_path", "load",
-    "fcirc_matvec", "fcirc_matvec_t", "fcirc_matvec_noalloc", "APlan", "poly_mul_int", "bigint_mul",
+    "fcirc_matvec", "fcirc_matvec_t", "fcirc_toeplitz_matvec", "fcirc_matvec_noalloc", "APlan", "poly_mul_int", "bigint_mul",
     "fcirc_matvec_c64", "fcirc_matvec_backward", "fcirc_layer",
     "fcirc_matvec_batched", "batched_autotune", "BatchedGraph", "sync_status", "release",
     "nth_root", "node_twiddle", "leaf_param", "twiddle_from_factor",
@@ -46,6 +46,7 @@ _SIGNATURES = {
     "fcirc_matvec": ([_u32, _u32, _vp, _vp, _vp, _u64, _vp], _i32),
     "fcirc_matvec_noalloc": ([_u32, _u32, _vp, _vp, _vp, _u64, _vp], _i32),
     "fcirc_matvec_t": ([_u32, _u32, _vp, _vp, _vp, _u64, _vp], _i32),
+    "fcirc_toeplitz_matvec": ([_u32, _vp, _vp, _vp, _u64, _vp], _i32),
     "fcirc_aplan_create": ([_u32, _u32, _vp, _u64, _vp, ctypes.POINTER(_vp)], _i32),
     "fcirc_matvec_aplan": ([_vp, _vp, _vp, _vp], _i32),
     "fcirc_aplan_destroy": ([_vp], _i32),
@@ -165,6 +166,25 @@ def fcirc_matvec_t(p: int, f: int, a, x, out=None, stream=None):
     st = _stream_handle(stream, a, x, out)
     _check(load().fcirc_matvec_t(p, f % p, a.data_ptr(), x.data_ptr(), out.data_ptr(), a.numel(), st),
            "fcirc_matvec_t")
+    return out
+
+
+def fcirc_toeplitz_matvec(p: int, t, x, out=None, stream=None):
+    """c = T x for the n x n Toeplitz matrix T[i][j] = t[j - i + n - 1]
+    (t: 2n - 1 diagonals, lowest first), by Corollary 1's embedding into a
+    power-of-two circulant (include/fcirc.h)."""
+    import torch
+    _u32_tensor(t, "t")
+    _u32_tensor(x, "x")
+    n = x.numel()
+    if x.dim() != 1 or t.dim() != 1 or t.numel() != 2 * n - 1:
+        raise ValueError("x must be 1-D of length n and t of length 2n - 1")
+    if out is None:
+        out = torch.empty_like(x)
+    _u32_tensor(out, "out")
+    st = _stream_handle(stream, t, x, out)
+    _check(load().fcirc_toeplitz_matvec(p, t.data_ptr(), x.data_ptr(), out.data_ptr(), n, st),
+           "fcirc_toeplitz_matvec")
     return out
 
 

@@ -282,6 +282,37 @@ static int matvec_core(const Plan *pl, const Src &sa, const Src &sx, uint32_t *d
     return FCIRC_OK;
 }
 
+// Corollary 1: an n x n product with n not a power of two (f-circulant with
+// row vector a, or Toeplitz with diagonals t[0 .. 2n-2]) as the first n
+// entries of an ordinary circulant product of size N >= 2n - 1 (a power of
+// two), built by k_embed.  `a` holds n (f-circulant) or 2n - 1 (Toeplitz)
+// words.
+static int embedded_matvec(uint32_t p, uint32_t f, const uint32_t *a, const uint32_t *x, uint32_t *c, uint64_t n,
+                           int toeplitz, cudaStream_t s)
+{
+    uint64_t N = 2;
+    while (N < 2 * n - 1) N <<= 1;
+    if (N > ((uint64_t)1 << kMaxLogN)) return fail(FCIRC_EINVAL, "n = %llu needs an embedding above 2^%d",
+                                                   (unsigned long long)n, kMaxLogN);
+    const PrimeTables *pt;
+    FCIRC_TRY(prime_tables(p, &pt));
+    const Plan *pl = nullptr;
+    FCIRC_TRY(get_plan(p, 1, N, &pl));
+    const uint64_t na = toeplitz ? 2 * n - 1 : n;
+    Arg aa{a, na * 4, true, false}, ax{x, n * 4, true, false}, ac{c, n * 4, false, true};
+    Staging st;
+    st.args = {&aa, &ax, &ac};
+    FCIRC_TRY(st.begin(s, 4 * N * 4));
+    const uint32_t *da = static_cast<const uint32_t *>(aa.d), *dx = static_cast<const uint32_t *>(ax.d);
+    uint32_t *ap = reinterpret_cast<uint32_t *>(st.scratch), *bp = ap + N, *cp = bp + N, *xs = cp + N;
+    const uint32_t fr = f % p;
+    FCIRC_TRY(launch_embed(toeplitz ? da + (n - 1) : da, da, dx, n, N, Tw{fr, host::shoup_quot(fr, p)}, p,
+                           toeplitz, ap, bp, s));
+    FCIRC_TRY(matvec_core(pl, Src{ap, N, SRC_U32, 1, pl->kt}, src_u32(bp, N), cp, xs, s));
+    FCIRC_CUDA_TRY(cudaMemcpyAsync(ac.d, cp, n * 4, cudaMemcpyDeviceToDevice, s));
+    return st.end();
+}
+
 // The three NTT-friendly primes of the polynomial and large-integer
 // products (2^23, 2^26 and 2^25 divide p - 1; their product exceeds 2^85).
 static const uint32_t kPrimes[3] = {998244353u, 469762049u, 167772161u};
@@ -375,8 +406,9 @@ int fcirc_matvec(uint32_t p, uint32_t f, const uint32_t *a, const uint32_t *x, u
 {
     set_error("");
     if (!a || !x || !c) return fail(FCIRC_EINVAL, "fcirc_matvec: null pointer");
-    if (!is_pow2(n)) return fail(FCIRC_EINVAL, "fcirc_matvec: n = %llu is not a power of two",
-                                 (unsigned long long)n);
+    if (n == 0) return fail(FCIRC_EINVAL, "fcirc_matvec: n = 0");
+    // n not a power of two: Corollary 1
+    if (!is_pow2(n)) return embedded_matvec(p, f, a, x, c, n, 0, static_cast<cudaStream_t>(stream));
     if (n > ((uint64_t)1 << kMaxLogN)) return fail(FCIRC_EINVAL, "fcirc_matvec: n above 2^%d", kMaxLogN);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const Plan *pl = nullptr;
@@ -402,6 +434,14 @@ int fcirc_matvec(uint32_t p, uint32_t f, const uint32_t *a, const uint32_t *x, u
     const Src sa{da, n, SRC_U32, 1, pl->kt};
     FCIRC_TRY(matvec_core(pl, sa, src_u32(dx, n), dc, reinterpret_cast<uint32_t *>(st.scratch), s));
     return st.end();
+}
+
+int fcirc_toeplitz_matvec(uint32_t p, const uint32_t *t, const uint32_t *x, uint32_t *c, uint64_t n, void *stream)
+{
+    set_error("");
+    if (!t || !x || !c) return fail(FCIRC_EINVAL, "fcirc_toeplitz_matvec: null pointer");
+    if (n == 0) return fail(FCIRC_EINVAL, "fcirc_toeplitz_matvec: n = 0");
+    return embedded_matvec(p, 0, t, x, c, n, 1, static_cast<cudaStream_t>(stream));
 }
 
 int fcirc_matvec_t(uint32_t p, uint32_t f, const uint32_t *a, const uint32_t *x, uint32_t *c, uint64_t n,

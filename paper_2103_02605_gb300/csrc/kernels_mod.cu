@@ -251,6 +251,38 @@ __global__ void k_rot_scale(const uint32_t *src, uint32_t *dst, uint64_t n, Tw f
         dst[j] = j + 1 < n ? reduce_once(shoup_mul(src[j + 1], f.w, f.wp, p), p) : src[0];
 }
 
+// Corollary 1 embedding of an n x n product into a power-of-two circulant of
+// size N >= 2n - 1 (parameter 1): a'[k] = u[k] for k < n, a'[N - m] = the
+// wrapped entry m (1 <= m < n), zero elsewhere; b' = x followed by zeros.
+// Wrapped entry m: f u[n - m] (f-circulant, toeplitz = 0) or t[n - 1 - m],
+// t the 2n - 1 diagonals of a Toeplitz matrix (toeplitz = 1, u = t + n - 1).
+__global__ void k_embed(const uint32_t *u, const uint32_t *t, const uint32_t *x, uint64_t n, uint64_t N, Tw f,
+                        uint32_t p, int toeplitz, uint32_t *ap, uint32_t *bp)
+{
+    for (uint64_t k = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; k < N; k += (uint64_t)gridDim.x * blockDim.x) {
+        uint32_t av = 0;
+        if (k < n) {
+            av = u[k];
+        } else if (k > N - n) {
+            const uint64_t m = N - k;   // 1 <= m < n
+            av = toeplitz ? t[n - 1 - m] : reduce_once(shoup_mul(u[n - m], f.w, f.wp, p), p);
+        }
+        ap[k] = av;
+        bp[k] = k < n ? x[k] : 0u;
+    }
+}
+
+int launch_embed(const uint32_t *u, const uint32_t *t, const uint32_t *x, uint64_t n, uint64_t N, Tw f, uint32_t p,
+                 int toeplitz, uint32_t *ap, uint32_t *bp, cudaStream_t s)
+{
+    unsigned blocks = (unsigned)((N + 255) / 256);
+    if (blocks > 152 * 8) blocks = 152 * 8;
+    ProfScope ps("k_embed", s);
+    k_embed<<<blocks, 256, 0, s>>>(u, t, x, n, N, f, p, toeplitz, ap, bp);
+    FCIRC_CUDA_TRY(cudaGetLastError());
+    return FCIRC_OK;
+}
+
 int launch_rot_scale(const uint32_t *src, uint32_t *dst, uint64_t n, Tw f, uint32_t p, cudaStream_t s)
 {
     unsigned blocks = (unsigned)((n + 255) / 256);

@@ -156,6 +156,8 @@ struct ColInvParams {
 int launch_tile(const TileParams &P, uint64_t ntiles, int njobs, cudaStream_t s);
 int launch_strided_fwd(const StrFwdParams &P, int njobs, cudaStream_t s);
 int launch_strided_inv(const StrInvParams &P, cudaStream_t s);
+int launch_embed(const uint32_t *u, const uint32_t *t, const uint32_t *x, uint64_t n, uint64_t N, Tw f, uint32_t p,
+                 int toeplitz, uint32_t *ap, uint32_t *bp, cudaStream_t s);
 int launch_rot_scale(const uint32_t *src, uint32_t *dst, uint64_t n, Tw f, uint32_t p, cudaStream_t s);
 int launch_crt_rot(const uint32_t *r1, const uint32_t *r2, const uint32_t *r3, uint64_t N,
                    uint64_t *out, uint64_t nout, const CrtConsts &C, cudaStream_t s);

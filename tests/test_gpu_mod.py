@@ -186,6 +186,38 @@ def test_matvec_transposed_large_by_evaluation(F, m):
         assert _eval_mod(c, pw, p) == ca * cx % p
 
 
+@pytest.mark.parametrize("n", [3, 5, 6, 7, 100, 1000, 4095, 5000, 70001, (1 << 20) + 3])
+def test_matvec_any_n_corollary1(F, orc, n):
+    """n not a power of two: Corollary 1's embedding into a power-of-two
+    circulant, any f (no roots of f needed), against the oracle."""
+    import torch
+    p = P1 if n % 2 else P3
+    g = I.SplitMix64(1100 + n)
+    a, x = g.uniform_mod(p, n), g.uniform_mod(p, n)
+    for f in (0, 1, p - 1, 12345):
+        c = F.fcirc_matvec(p, f, dev_u32(a), dev_u32(x))
+        torch.cuda.synchronize()
+        got = host_u32(c)
+        if n <= 5000:
+            assert np.array_equal(got, orc.fcirc_matvec_mod(p, f, a, x)), (n, f)
+        else:
+            rows = sample_rows(n, seed=n % 1000)
+            assert np.array_equal(got[rows.astype(np.int64)], orc.fcirc_matvec_mod_rows(p, f, a, x, rows)), (n, f)
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 64, 1000, 4097])
+def test_toeplitz_vs_oracle(F, orc, n):
+    import torch
+    g = I.SplitMix64(1200 + n)
+    t, x = g.uniform_mod(P2, 2 * n - 1), g.uniform_mod(P2, n)
+    c = F.fcirc_toeplitz_matvec(P2, dev_u32(t), dev_u32(x))
+    torch.cuda.synchronize()
+    assert np.array_equal(host_u32(c), orc.toeplitz_matvec_mod(P2, t, x))
+    # host buffers
+    ch = F.fcirc_toeplitz_matvec(P2, torch.from_numpy(t.view(np.int32)), torch.from_numpy(x.view(np.int32)))
+    assert np.array_equal(ch.numpy().view(np.uint32), host_u32(c))
+
+
 def test_matvec_config0_full(F, orc):
     """n = 2^12, f = 1, p = 998244353: the single-instance workload, full vector."""
     a, x = I.single_mod(1 << 12)
@@ -234,9 +266,10 @@ def test_matvec_errors(F):
     with pytest.raises(F.FcircError) as e:
         F.fcirc_matvec(P1, 1, big, big)      # needs a 2^24-th root of unity
     assert e.value.status == 2
-    odd = torch.zeros(6, dtype=torch.int32, device="cuda")
+    # n = 6 is no error (Corollary 1), n = 0 is
+    z0 = torch.zeros(0, dtype=torch.int32, device="cuda")
     with pytest.raises(F.FcircError) as e:
-        F.fcirc_matvec(P1, 1, odd, odd)
+        F.fcirc_matvec(P1, 1, z0, z0)
     assert e.value.status == 1
     L = F.load()
     assert L.fcirc_matvec(P1, 1, None, None, None, 8, None) == 1

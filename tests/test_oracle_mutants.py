@@ -42,6 +42,9 @@ MUTANTS = {
     # column convention: wrapped terms indexed without the wrap
     "t_wrong_wrap": ("wrapped = (wrapped + mulmod_u64(a[m], x[j + n - m], p)) % p;",
                      "wrapped = (wrapped + mulmod_u64(a[m], x[m - j - 1], p)) % p;"),
+    # Toeplitz: diagonal index mirrored
+    "toeplitz_mirror": ("acc = (acc + mulmod_u64(t[j + n - 1 - i], x[j], p)) % p;",
+                        "acc = (acc + mulmod_u64(t[i + n - 1 - j], x[j], p)) % p;"),
     # off-by-one in the polynomial product window
     "poly_window": ("for (uint64_t i = lo; i <= hi; ++i)\n        s +=",
                     "for (uint64_t i = lo + 1; i <= hi; ++i)\n        s +="),
@@ -61,6 +64,7 @@ PIN_CALLS = [
     lambda o: pins.test_general_f_by_diagonal_scaling_fft(o, 8, 2.0),
     lambda o: pins.test_transpose_is_polynomial_product_mod_xn_minus_f(o, 8),
     lambda o: pins.test_column_convention_is_the_transpose(o, 8),
+    lambda o: pins.test_toeplitz_oracle(o, 6),
     lambda o: pins.test_algorithm1_bruteforce_equals_dense(o, 16, None),
     lambda o: pins.test_complex_gradients_finite_differences(o, 0.6 + 0.8j),
     lambda o: pins.test_complex_gradients_finite_differences(o, 2.0 - 0.5j),

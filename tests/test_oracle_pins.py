@@ -216,6 +216,26 @@ def test_column_convention_is_the_transpose(orc, n):
     assert np.array_equal(orc.fcirc_matvec_t_mod(P, f, a, e0), a)
 
 
+@pytest.mark.parametrize("n", [1, 2, 3, 6, 11])
+def test_toeplitz_oracle(orc, n):
+    """The Toeplitz oracle against a Python dense product, and against the
+    f-circulant oracle for the Toeplitz matrix an f-circulant is (diagonal
+    k >= 0 holds a_k, diagonal -m holds f a_{n-m}, Definition 2)."""
+    rng = np.random.default_rng(500 + n)
+    t = rand_mod(rng, 2 * n - 1)
+    x = rand_mod(rng, n)
+    want = [sum(int(t[j - i + n - 1]) * int(x[j]) for j in range(n)) % P for i in range(n)]
+    assert [int(v) for v in orc.toeplitz_matvec_mod(P, t, x)] == want
+    a = rand_mod(rng, n)
+    f = int(rng.integers(1, P))
+    tc = np.zeros(2 * n - 1, np.uint32)
+    for k in range(n):
+        tc[n - 1 + k] = a[k]
+    for m in range(1, n):
+        tc[n - 1 - m] = f * int(a[n - m]) % P
+    assert np.array_equal(orc.toeplitz_matvec_mod(P, tc, x), orc.fcirc_matvec_mod(P, f, a, x))
+
+
 # -- the paper's Algorithm 1 (brute force) agrees with the dense oracle ----------
 
 @pytest.mark.parametrize("n", [1, 2, 4, 8, 16, 32])
