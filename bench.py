@@ -375,6 +375,18 @@ def run_extras(F, I, dev, stream):
                                    "speedup_vs_per_instance": pm / bm, "Gelem_s": int(off[-1]) / (bm * 1e-3) / 1e9,
                                    "autotuned_config": {"index": tuned[0], "ctas_per_sm": tuned[1],
                                                         "tile_log": tuned[2]}}
+    # the paper's own field GF(p^2), p = 2^31 - 1: 10,000 circulant products
+    # of size 2048 with f = 1 (the shape of the paper's timing experiment:
+    # 10,000 products of polynomials of 1024 coefficients each)
+    gb, gn = 10000, 2048
+    ga = torch.randint(0, (1 << 31) - 1, (gb, gn, 2), dtype=torch.int32, device=dev,
+                       generator=torch.Generator(device=dev).manual_seed(I.SEED_BASE + 5))
+    gx = torch.randint(0, (1 << 31) - 1, (gb, gn, 2), dtype=torch.int32, device=dev,
+                       generator=torch.Generator(device=dev).manual_seed(I.SEED_BASE + 6))
+    gc = torch.empty_like(ga)
+    gm, gmin = _time(lambda: F.fcirc_matvec_gf(ga, gx, (1, 0), out=gc, stream=stream), 10, flush, stream)
+    out["gfp2_10000x2048"] = {"ms": gm, "ms_min": gmin, "Gelem_s": gb * gn / (gm * 1e-3) / 1e9}
+    del ga, gx, gc
     # large integers: two 2^26-bit operands
     A, B = I.bigint_pair()
     tA = torch.from_numpy(A.view(np.int16)).to(dev)

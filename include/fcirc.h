@@ -296,6 +296,27 @@ int fcirc_matvec_c64(const float *a, const float *x, float *c, double f_re, doub
                      uint64_t n, uint64_t batch, void *stream);
 
 /*
+ * fcirc_matvec_gf -- a batch of f-circulant products over the paper's own
+ * field GF(p^2) = Z/pZ[sqrt 3], p = 2^31 - 1 (Section 3.1: p + 1 = 2^31, and
+ * 2 + sqrt 3 generates the elements of order dividing p + 1, so the
+ * power-of-two roots of unity Algorithm 1 needs exist up to order 2^31).
+ * Same recursion and batch layout as fcirc_matvec_c64, exact arithmetic
+ * with Mersenne reduction.
+ *
+ *   a, x, c  batch instances of n elements, each an interleaved (re, im)
+ *            uint32 pair meaning re + im sqrt 3, canonical in [0, p);
+ *            instance b at offset 2 n b words.  Results canonical.
+ *   f        f_re + f_im sqrt 3, canonical, with a 2^(log2 n - 1)-th root
+ *            (Theorem 1); f = 1 gives ordinary circulants, the paper's
+ *            polynomial products.
+ *   n        a power of two, 8 <= n <= 4096;  batch >= 0.
+ * Errors: FCIRC_EINVAL for null pointers, an unsupported n or a
+ * non-canonical f; FCIRC_ENOROOT for f = 0 or f without the root.
+ */
+int fcirc_matvec_gf(const uint32_t *a, const uint32_t *x, uint32_t *c, uint32_t f_re, uint32_t f_im,
+                    uint64_t n, uint64_t batch, void *stream);
+
+/*
  * fcirc_matvec_backward -- gradients of the real loss L = Re <g, A x> (the
  * convention PyTorch uses for complex tensors: the gradient of z is
  * dL/dRe z + i dL/dIm z), for the same batch layout as fcirc_matvec_c64:

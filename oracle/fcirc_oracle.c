@@ -110,6 +110,41 @@ void oracle_fcirc_matvec_t_mod(uint32_t p, uint32_t f, const uint32_t *a,
     }
 }
 
+/* The product over the paper's field GF(p^2) = Z/pZ[sqrt 3], p = 2^31 - 1
+ * (Section 3.1): elements (re, im) = re + im sqrt 3 stored as uint32 pairs,
+ * c[i] = sum_k a[k] x[(i+k) mod n] f^[i+k >= n] (Definition 2). */
+#define GFP 2147483647ull
+static void gf_mul(uint64_t ar, uint64_t ai, uint64_t br, uint64_t bi, uint64_t *cr, uint64_t *ci)
+{
+    *cr = (ar * br % GFP + 3 * (ai * bi % GFP)) % GFP;
+    *ci = (ar * bi % GFP + ai * br % GFP) % GFP;
+}
+
+void oracle_fcirc_matvec_gf(uint32_t f_re, uint32_t f_im, const uint32_t *a, const uint32_t *x, uint32_t *c,
+                            uint64_t n)
+{
+    #pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t ii = 0; ii < (int64_t)n; ++ii) {
+        const uint64_t i = (uint64_t)ii;
+        uint64_t ur = 0, ui = 0, lr = 0, li = 0, pr, pi;
+        for (uint64_t k = 0; k < n; ++k) {
+            const uint64_t j = i + k;
+            if (j < n) {
+                gf_mul(a[2 * k], a[2 * k + 1], x[2 * j], x[2 * j + 1], &pr, &pi);
+                ur = (ur + pr) % GFP;
+                ui = (ui + pi) % GFP;
+            } else {
+                gf_mul(a[2 * k], a[2 * k + 1], x[2 * (j - n)], x[2 * (j - n) + 1], &pr, &pi);
+                lr = (lr + pr) % GFP;
+                li = (li + pi) % GFP;
+            }
+        }
+        gf_mul(f_re, f_im, lr, li, &pr, &pi);
+        c[2 * i] = (uint32_t)((ur + pr) % GFP);
+        c[2 * i + 1] = (uint32_t)((ui + pi) % GFP);
+    }
+}
+
 /* Toeplitz product c = T x, T[i][j] = t[j - i + n - 1] (t: the 2n - 1
  * diagonals, lowest first), straight from the definition. */
 void oracle_toeplitz_matvec_mod(uint32_t p, const uint32_t *t, const uint32_t *x, uint32_t *c, uint64_t n)

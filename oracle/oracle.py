@@ -57,6 +57,7 @@ def lib():
             L.oracle_fcirc_matvec_mod_rows.argtypes = [U32, U32, u32p, u32p, U64, u64p, U64, u32p]
             L.oracle_fcirc_matvec_t_mod.argtypes = [U32, U32, u32p, u32p, u32p, U64]
             L.oracle_toeplitz_matvec_mod.argtypes = [U32, u32p, u32p, u32p, U64]
+            L.oracle_fcirc_matvec_gf.argtypes = [U32, U32, u32p, u32p, u32p, U64]
             L.oracle_fcirc_matvec_mod_batched.argtypes = [U32, u32p, u64p, u32p, u32p, u32p, U32]
             L.oracle_fcirc_matvec_c128.argtypes = [F64, F64, f64p, f64p, f64p, U64, U64]
             L.oracle_fcirc_grad_c128.argtypes = [F64, F64, f64p, f64p, f64p, f64p, f64p, U64, U64]
@@ -110,6 +111,25 @@ def toeplitz_matvec_mod(p: int, t, x) -> np.ndarray:
     c = np.empty_like(x)
     lib().oracle_toeplitz_matvec_mod(p, t, x, c, x.size)
     return c
+
+
+GF_P = (1 << 31) - 1
+
+
+def fcirc_matvec_gf(f, a, x) -> np.ndarray:
+    """Over GF(p^2) = Z/pZ[sqrt 3], p = 2^31 - 1: a, x of shape (n, 2) or
+    (batch, n, 2) holding (re, im); f = (f_re, f_im).  Dense definition."""
+    a, x = _u32(a), _u32(x)
+    assert a.shape == x.shape and a.shape[-1] == 2
+    flat_a, flat_x = a.reshape(-1, a.shape[-2], 2), x.reshape(-1, x.shape[-2], 2)
+    out = np.empty_like(flat_a)
+    for b in range(flat_a.shape[0]):
+        ab, xb = np.ascontiguousarray(flat_a[b]), np.ascontiguousarray(flat_x[b])
+        cb = np.empty_like(ab)
+        lib().oracle_fcirc_matvec_gf(int(f[0]) % GF_P, int(f[1]) % GF_P, ab.reshape(-1), xb.reshape(-1),
+                                     cb.reshape(-1), ab.shape[0])
+        out[b] = cb
+    return out.reshape(a.shape)
 
 
 def fcirc_matvec_mod_rows(p: int, f: int, a, x, rows) -> np.ndarray:

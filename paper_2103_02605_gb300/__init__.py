@@ -26,7 +26,7 @@ from . import build as _build
 
 __all__ = [
     "FcircError", "library_path", "load",
-    "fcirc_matvec", "fcirc_matvec_t", "fcirc_toeplitz_matvec", "fcirc_matvec_noalloc", "APlan", "poly_mul_int", "bigint_mul",
+    "fcirc_matvec", "fcirc_matvec_t", "fcirc_toeplitz_matvec", "fcirc_matvec_gf", "GF_P", "fcirc_matvec_noalloc", "APlan", "poly_mul_int", "bigint_mul",
     "fcirc_matvec_c64", "fcirc_matvec_backward", "fcirc_layer",
     "fcirc_matvec_batched", "batched_autotune", "BatchedGraph", "sync_status", "release",
     "nth_root", "node_twiddle", "leaf_param", "twiddle_from_factor",
@@ -35,6 +35,7 @@ __all__ = [
 ]
 
 PRIMES = (998244353, 469762049, 167772161)
+GF_P = (1 << 31) - 1   # the paper's field GF(p^2) = Z/pZ[sqrt 3]
 
 _lock = threading.Lock()
 _lib = None
@@ -47,6 +48,7 @@ _SIGNATURES = {
     "fcirc_matvec_noalloc": ([_u32, _u32, _vp, _vp, _vp, _u64, _vp], _i32),
     "fcirc_matvec_t": ([_u32, _u32, _vp, _vp, _vp, _u64, _vp], _i32),
     "fcirc_toeplitz_matvec": ([_u32, _vp, _vp, _vp, _u64, _vp], _i32),
+    "fcirc_matvec_gf": ([_vp, _vp, _vp, _u32, _u32, _u64, _u64, _vp], _i32),
     "fcirc_aplan_create": ([_u32, _u32, _vp, _u64, _vp, ctypes.POINTER(_vp)], _i32),
     "fcirc_matvec_aplan": ([_vp, _vp, _vp, _vp], _i32),
     "fcirc_aplan_destroy": ([_vp], _i32),
@@ -185,6 +187,27 @@ def fcirc_toeplitz_matvec(p: int, t, x, out=None, stream=None):
     st = _stream_handle(stream, t, x, out)
     _check(load().fcirc_toeplitz_matvec(p, t.data_ptr(), x.data_ptr(), out.data_ptr(), n, st),
            "fcirc_toeplitz_matvec")
+    return out
+
+
+def fcirc_matvec_gf(a, x, f=(1, 0), out=None, stream=None):
+    """Batched f-circulant products over GF(p^2) = Z/pZ[sqrt 3], p = 2^31 - 1
+    (the paper's field).  a, x: int32/uint32 tensors of shape (batch, n, 2)
+    holding (re, im) = re + im sqrt 3; f = (f_re, f_im).  8 <= n <= 4096."""
+    import torch
+    for t, nm in ((a, "a"), (x, "x")):
+        _u32_tensor(t, nm)
+        if t.dim() != 3 or t.shape[2] != 2:
+            raise ValueError(f"{nm} must have shape (batch, n, 2)")
+    if a.shape != x.shape:
+        raise ValueError("a and x must have the same shape")
+    batch, n = a.shape[0], a.shape[1]
+    if out is None:
+        out = torch.empty_like(a)
+    _u32_tensor(out, "out")
+    st = _stream_handle(stream, a, x, out)
+    _check(load().fcirc_matvec_gf(a.data_ptr(), x.data_ptr(), out.data_ptr(), int(f[0]) % GF_P, int(f[1]) % GF_P,
+                                  n, batch, st), "fcirc_matvec_gf")
     return out
 
 

@@ -18,6 +18,7 @@
 #include "kernels_complex.hpp"
 #include "kernels_mod.hpp"
 #include "prof.hpp"
+#include "gfp2.hpp"
 #include "ring.hpp"
 
 namespace fcirc {
@@ -708,6 +709,35 @@ int fcirc_matvec_c64(const float *a, const float *x, float *c, double f_re, doub
     P.batch = batch;
     P.scale = std::ldexp(1.0f, -(m - 1));
     FCIRC_TRY(launch_cfwd(P, m, s));
+    return st.end();
+}
+
+int fcirc_matvec_gf(const uint32_t *a, const uint32_t *x, uint32_t *c, uint32_t f_re, uint32_t f_im, uint64_t n,
+                    uint64_t batch, void *stream)
+{
+    set_error("");
+    if (!a || !x || !c) return fail(FCIRC_EINVAL, "fcirc_matvec_gf: null pointer");
+    if (!is_pow2(n) || n < 8 || n > 4096)
+        return fail(FCIRC_EINVAL, "fcirc_matvec_gf: n = %llu must be a power of two in [8, 4096]",
+                    (unsigned long long)n);
+    if (f_re >= gf::P || f_im >= gf::P) return fail(FCIRC_EINVAL, "fcirc_matvec_gf: f not canonical");
+    if (f_re == 0 && f_im == 0) return fail(FCIRC_ENOROOT, "fcirc_matvec_gf: f = 0 has no inverse");
+    if (batch == 0) return FCIRC_OK;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const int m = ilog2(n);
+    GParams P{};
+    FCIRC_TRY(gf_tables(f_re, f_im, n, &P.tw, &P.itw));
+    const size_t bytes = n * batch * 8;
+    Arg aa{a, bytes, true, false}, ax{x, bytes, true, false}, ac{c, bytes, false, true};
+    Staging st;
+    st.args = {&aa, &ax, &ac};
+    FCIRC_TRY(st.begin(s, 0));
+    P.a = static_cast<const uint32_t *>(aa.d);
+    P.x = static_cast<const uint32_t *>(ax.d);
+    P.c = static_cast<uint32_t *>(ac.d);
+    P.batch = batch;
+    P.scale = gf::inv(gf::E{(uint32_t)1u << (m - 1), 0u}).re;   // 2^-L, L = m - 1
+    FCIRC_TRY(launch_gfwd(P, m, s));
     return st.end();
 }
 

@@ -505,7 +505,8 @@ __device__ __forceinline__ void c4inv_stage(const ColInvParams &P, uint32_t *sm,
 
 // CRT phase of the polynomial product: the rows of the store phase, the three
 // primes' canonical residues from the CTA that computed them, Garner's CRT,
-// and the int64 coefficient stored rotated by one (c_k = d_{k+1}).
+// and the int64 coefficient stored rotated by one (coefficient k is circulant
+// entry k + 1).
 template <int LF>
 __device__ __forceinline__ void c4_crt_phase(const ColInvParams &P, const uint32_t *sm, uint32_t base0, int logS,
                                              int rank, int tid)
@@ -524,7 +525,7 @@ __device__ __forceinline__ void c4_crt_phase(const ColInvParams &P, const uint32
         const uint4 r2 = c4_seg_ld<LF>(sb + PB, cq, row);
         const uint4 r3 = c4_seg_ld<LF>(sb + 2 * PB, cq, row);
         const uint32_t idx = base0 + ((uint32_t)cq << 2) + ((uint32_t)row << logS);
-        const uint32_t d0 = (idx + mask) & mask;   // c_k = d_{k+1}
+        const uint32_t d0 = (idx + mask) & mask;   // coefficient k is circulant entry k + 1
         if (d0 < P.nout) P.dst64[d0] = crt3(r1.x, r2.x, r3.x, P.crt);
         if (idx < P.nout) P.dst64[idx] = crt3(r1.y, r2.y, r3.y, P.crt);
         if (idx + 1 < P.nout) P.dst64[idx + 1] = crt3(r1.z, r2.z, r3.z, P.crt);
@@ -575,7 +576,8 @@ __global__ void __cluster_dims__(C4<LF>::CL, 1, 1) __launch_bounds__(kC4Threads,
 // shared memory (so two clusters' CTAs share an SM and overlap their memory
 // and arithmetic phases); then each CTA takes a third of the group's rows,
 // gathers the three canonical residues through distributed shared memory,
-// and writes the CRT result rotated by one (c_k = d_{k+1}).
+// and writes the CRT result rotated by one (coefficient k is circulant entry
+// k + 1).
 template <int LF>
 __global__ void __cluster_dims__(3, 1, 1) __launch_bounds__(kC4Threads, 2)
     k_colinv4x3(const __grid_constant__ ColInvParams P)

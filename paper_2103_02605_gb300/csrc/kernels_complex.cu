@@ -30,6 +30,7 @@
 #include "common.hpp"
 #include "kernels_complex.hpp"
 #include "prof.hpp"
+#include "gfp2.hpp"
 #include "ring.hpp"
 
 namespace fcirc {
@@ -45,6 +46,15 @@ __device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(
 __device__ __forceinline__ float2 cconj(float2 a) { return make_float2(a.x, -a.y); }
 __device__ __forceinline__ float2 cneg(float2 a) { return make_float2(-a.x, -a.y); }
 
+// The same four operations in GF(p^2) = Z/pZ[sqrt 3], p = 2^31 - 1 (the
+// paper's own field, Section 3.1), an element (x, y) = x + y sqrt 3.
+__device__ __forceinline__ uint2 gf2(gf::E e) { return make_uint2(e.re, e.im); }
+__device__ __forceinline__ gf::E gfe(uint2 v) { return gf::E{v.x, v.y}; }
+__device__ __forceinline__ uint2 cmul(uint2 a, uint2 b) { return gf2(gf::mul(gfe(a), gfe(b))); }
+__device__ __forceinline__ uint2 cadd(uint2 a, uint2 b) { return gf2(gf::add(gfe(a), gfe(b))); }
+__device__ __forceinline__ uint2 csub(uint2 a, uint2 b) { return gf2(gf::sub(gfe(a), gfe(b))); }
+__device__ __forceinline__ uint2 cneg(uint2 a) { return gf2(gf::neg(gfe(a))); }
+
 template <int M>
 struct CShape {
     static constexpr int N = 1 << M;
@@ -59,14 +69,18 @@ struct CShape {
 };
 
 // One product's data in shared memory: row-vector side R and vector side X.
-struct Side {
-    float2 *R, *X;
-    const float2 *tw, *itw;   // heap-indexed twiddles and inverses, [N/2]
+// T: float2 (complex FP32) or uint2 (GF(p^2), gfp2.hpp); the arithmetic
+// comes from the cmul / cadd / csub / cneg overloads.
+template <class T>
+struct SideT {
+    T *R, *X;
+    const T *tw, *itw;   // heap-indexed twiddles and inverses, [N/2]
 };
+using Side = SideT<float2>;
 
 // forward stage S (levels d0 .. d0+nl-1) on both sides
-template <int M, int S>
-__device__ __forceinline__ void cfwd_stage(Side &sd, int t)
+template <int M, int S, class T>
+__device__ __forceinline__ void cfwd_stage(SideT<T> &sd, int t)
 {
     using Sh = CShape<M>;
     constexpr int NL = Sh::nl(S), D0 = Sh::d0(S), G = 8 >> NL, MM = 1 << NL;
@@ -76,7 +90,7 @@ __device__ __forceinline__ void cfwd_stage(Side &sd, int t)
         const int gg = t + Sh::NTI * h;
         const int blk = gg >> LST, off = gg & ((1 << LST) - 1);
         const int e0 = (blk << LRB) + off;
-        float2 r[MM], x[MM];
+        T r[MM], x[MM];
 #pragma unroll
         for (int i = 0; i < MM; ++i) {
             r[i] = sd.R[e0 + (i << LST)];
@@ -87,15 +101,15 @@ __device__ __forceinline__ void cfwd_stage(Side &sd, int t)
             const int hh = MM >> (d + 1);
 #pragma unroll
             for (int j = 0; j < (1 << d); ++j) {
-                const float2 s = __ldg(&sd.tw[(1 << (D0 + d)) + (blk << d) + j]);
+                const T s = __ldg(&sd.tw[(1 << (D0 + d)) + (blk << d) + j]);
 #pragma unroll
                 for (int i = 0; i < hh; ++i) {
                     const int lo = (j << (NL - d)) + i, hi = lo + hh;
-                    const float2 tr = cmul(s, r[hi]);
-                    const float2 tx = cmul(s, x[lo]);
+                    const T tr = cmul(s, r[hi]);
+                    const T tx = cmul(s, x[lo]);
                     r[hi] = csub(r[lo], tr);
                     r[lo] = cadd(r[lo], tr);
-                    const float2 xh = x[hi];
+                    const T xh = x[hi];
                     x[hi] = csub(tx, xh);
                     x[lo] = cadd(tx, xh);
                 }
@@ -110,8 +124,8 @@ __device__ __forceinline__ void cfwd_stage(Side &sd, int t)
 }
 
 // recombination stage S (levels d0+nl-1 .. d0), result in R
-template <int M, int S>
-__device__ __forceinline__ void crec_stage(Side &sd, int t)
+template <int M, int S, class T>
+__device__ __forceinline__ void crec_stage(SideT<T> &sd, int t)
 {
     using Sh = CShape<M>;
     constexpr int NL = Sh::nl(S), D0 = Sh::d0(S), G = 8 >> NL, MM = 1 << NL;
@@ -121,7 +135,7 @@ __device__ __forceinline__ void crec_stage(Side &sd, int t)
         const int gg = t + Sh::NTI * h;
         const int blk = gg >> LST, off = gg & ((1 << LST) - 1);
         const int e0 = (blk << LRB) + off;
-        float2 r[MM];
+        T r[MM];
 #pragma unroll
         for (int i = 0; i < MM; ++i) r[i] = sd.R[e0 + (i << LST)];
 #pragma unroll
@@ -129,11 +143,11 @@ __device__ __forceinline__ void crec_stage(Side &sd, int t)
             const int hh = MM >> (d + 1);
 #pragma unroll
             for (int j = 0; j < (1 << d); ++j) {
-                const float2 si = __ldg(&sd.itw[(1 << (D0 + d)) + (blk << d) + j]);
+                const T si = __ldg(&sd.itw[(1 << (D0 + d)) + (blk << d) + j]);
 #pragma unroll
                 for (int i = 0; i < hh; ++i) {
                     const int lo = (j << (NL - d)) + i, hi = lo + hh;
-                    const float2 sum = cadd(r[lo], r[hi]);
+                    const T sum = cadd(r[lo], r[hi]);
                     r[hi] = csub(r[lo], r[hi]);
                     r[lo] = cmul(sum, si);
                 }
@@ -146,24 +160,24 @@ __device__ __forceinline__ void crec_stage(Side &sd, int t)
 
 // last stage: 8 contiguous numbers at 8t: levels L-2, L-1, four 2x2
 // leaves, recombination L-1, L-2; result in R
-template <int M>
-__device__ __forceinline__ void cleaf_stage(Side &sd, int t)
+template <int M, class T>
+__device__ __forceinline__ void cleaf_stage(SideT<T> &sd, int t)
 {
     constexpr int L = M - 1;
-    float2 r[8], x[8];
+    T r[8], x[8];
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
         r[i] = sd.R[8 * t + i];
         x[i] = sd.X[8 * t + i];
     }
-    const float2 s0 = __ldg(&sd.tw[(1 << (L - 2)) + t]);
-    const float2 s1[2] = {__ldg(&sd.tw[(1 << (L - 1)) + 2 * t]), __ldg(&sd.tw[(1 << (L - 1)) + 2 * t + 1])};
+    const T s0 = __ldg(&sd.tw[(1 << (L - 2)) + t]);
+    const T s1[2] = {__ldg(&sd.tw[(1 << (L - 1)) + 2 * t]), __ldg(&sd.tw[(1 << (L - 1)) + 2 * t + 1])};
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
-        const float2 tr = cmul(s0, r[i + 4]), tx = cmul(s0, x[i]);
+        const T tr = cmul(s0, r[i + 4]), tx = cmul(s0, x[i]);
         r[i + 4] = csub(r[i], tr);
         r[i] = cadd(r[i], tr);
-        const float2 xh = x[i + 4];
+        const T xh = x[i + 4];
         x[i + 4] = csub(tx, xh);
         x[i] = cadd(tx, xh);
     }
@@ -172,36 +186,36 @@ __device__ __forceinline__ void cleaf_stage(Side &sd, int t)
 #pragma unroll
         for (int i = 0; i < 2; ++i) {
             const int lo = 4 * hb + i, hi = lo + 2;
-            const float2 tr = cmul(s1[hb], r[hi]), tx = cmul(s1[hb], x[lo]);
+            const T tr = cmul(s1[hb], r[hi]), tx = cmul(s1[hb], x[lo]);
             r[hi] = csub(r[lo], tr);
             r[lo] = cadd(r[lo], tr);
-            const float2 xh = x[hi];
+            const T xh = x[hi];
             x[hi] = csub(tx, xh);
             x[lo] = cadd(tx, xh);
         }
     // leaves (2q, 2q+1): the phi-circulant [[a0, a1], [phi a1, a0]], phi = +-s_{L-1}
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-        const float2 phi = (q & 1) ? cneg(s1[q >> 1]) : s1[q >> 1];
-        const float2 a0 = r[2 * q], a1 = r[2 * q + 1], y0 = x[2 * q], y1 = x[2 * q + 1];
-        const float2 a1f = cmul(phi, a1);
+        const T phi = (q & 1) ? cneg(s1[q >> 1]) : s1[q >> 1];
+        const T a0 = r[2 * q], a1 = r[2 * q + 1], y0 = x[2 * q], y1 = x[2 * q + 1];
+        const T a1f = cmul(phi, a1);
         r[2 * q] = cadd(cmul(a0, y0), cmul(a1, y1));
         r[2 * q + 1] = cadd(cmul(a1f, y0), cmul(a0, y1));
     }
-    const float2 i1[2] = {__ldg(&sd.itw[(1 << (L - 1)) + 2 * t]), __ldg(&sd.itw[(1 << (L - 1)) + 2 * t + 1])};
-    const float2 i0 = __ldg(&sd.itw[(1 << (L - 2)) + t]);
+    const T i1[2] = {__ldg(&sd.itw[(1 << (L - 1)) + 2 * t]), __ldg(&sd.itw[(1 << (L - 1)) + 2 * t + 1])};
+    const T i0 = __ldg(&sd.itw[(1 << (L - 2)) + t]);
 #pragma unroll
     for (int hb = 0; hb < 2; ++hb)
 #pragma unroll
         for (int i = 0; i < 2; ++i) {
             const int lo = 4 * hb + i, hi = lo + 2;
-            const float2 sum = cadd(r[lo], r[hi]);
+            const T sum = cadd(r[lo], r[hi]);
             r[hi] = csub(r[lo], r[hi]);
             r[lo] = cmul(sum, i1[hb]);
         }
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
-        const float2 sum = cadd(r[i], r[i + 4]);
+        const T sum = cadd(r[i], r[i + 4]);
         r[i + 4] = csub(r[i], r[i + 4]);
         r[i] = cmul(sum, i0);
     }
@@ -210,33 +224,33 @@ __device__ __forceinline__ void cleaf_stage(Side &sd, int t)
 }
 
 // whole product for one instance: forward stages, last stage, recombination
-template <int M, int S>
-__device__ __forceinline__ void cfwd_all(Side &sd, int t)
+template <int M, int S, class T>
+__device__ __forceinline__ void cfwd_all(SideT<T> &sd, int t)
 {
     if constexpr (S < CShape<M>::NST) {
-        cfwd_stage<M, S>(sd, t);
+        cfwd_stage<M, S, T>(sd, t);
         __syncthreads();
-        cfwd_all<M, S + 1>(sd, t);
+        cfwd_all<M, S + 1, T>(sd, t);
     }
 }
 
-template <int M, int S>
-__device__ __forceinline__ void crec_all(Side &sd, int t)
+template <int M, int S, class T>
+__device__ __forceinline__ void crec_all(SideT<T> &sd, int t)
 {
     if constexpr (S >= 0) {
-        crec_stage<M, S>(sd, t);
+        crec_stage<M, S, T>(sd, t);
         __syncthreads();
-        crec_all<M, S - 1>(sd, t);
+        crec_all<M, S - 1, T>(sd, t);
     }
 }
 
-template <int M>
-__device__ __forceinline__ void cproduct(Side &sd, int t)
+template <int M, class T>
+__device__ __forceinline__ void cproduct(SideT<T> &sd, int t)
 {
-    cfwd_all<M, 0>(sd, t);
-    cleaf_stage<M>(sd, t);
+    cfwd_all<M, 0, T>(sd, t);
+    cleaf_stage<M, T>(sd, t);
     __syncthreads();
-    crec_all<M, CShape<M>::NST - 1>(sd, t);
+    crec_all<M, CShape<M>::NST - 1, T>(sd, t);
 }
 
 template <int M>
@@ -257,7 +271,7 @@ __global__ void __launch_bounds__(CShape<M>::CT) k_cfwd(const __grid_constant__ 
         sd.X[e] = live ? x[e] : make_float2(0.f, 0.f);
     }
     __syncthreads();
-    cproduct<M>(sd, t);
+    cproduct<M, float2>(sd, t);
     if (live) {
         float2 *c = reinterpret_cast<float2 *>(P.c) + inst * Sh::N;
 #pragma unroll
@@ -265,6 +279,38 @@ __global__ void __launch_bounds__(CShape<M>::CT) k_cfwd(const __grid_constant__ 
             const int e = t + Sh::NTI * k;
             const float2 v = sd.R[e];
             c[e] = make_float2(v.x * P.scale, v.y * P.scale);
+        }
+    }
+}
+
+// Products over GF(p^2): the same recursion and layout, uint2 elements; the
+// deferred halvings are one multiplication by 2^-L mod p at the end.
+template <int M>
+__global__ void __launch_bounds__(CShape<M>::CT) k_gfwd(const __grid_constant__ GParams P)
+{
+    using Sh = CShape<M>;
+    extern __shared__ __align__(16) uint2 gsm[];
+    const int li = threadIdx.x / Sh::NTI, t = threadIdx.x % Sh::NTI;
+    const uint64_t inst = (uint64_t)blockIdx.x * Sh::IPC + li;
+    const bool live = inst < P.batch;
+    SideT<uint2> sd{gsm + (size_t)li * 2 * Sh::N, gsm + (size_t)li * 2 * Sh::N + Sh::N, P.tw, P.itw};
+    const uint2 *a = reinterpret_cast<const uint2 *>(P.a) + inst * Sh::N;
+    const uint2 *x = reinterpret_cast<const uint2 *>(P.x) + inst * Sh::N;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        const int e = t + Sh::NTI * k;
+        sd.R[e] = live ? a[e] : make_uint2(0u, 0u);
+        sd.X[e] = live ? x[e] : make_uint2(0u, 0u);
+    }
+    __syncthreads();
+    cproduct<M, uint2>(sd, t);
+    if (live) {
+        uint2 *c = reinterpret_cast<uint2 *>(P.c) + inst * Sh::N;
+        const uint2 sc = make_uint2(P.scale, 0u);
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            const int e = t + Sh::NTI * k;
+            c[e] = cmul(sd.R[e], sc);
         }
     }
 }
@@ -298,8 +344,8 @@ __global__ void __launch_bounds__(CShape<M>::CT) k_cbwd(const __grid_constant__ 
         sa.X[e] = live ? cconj(x[e]) : z;
     }
     __syncthreads();
-    cproduct<M>(sx, t);
-    cproduct<M>(sa, t);
+    cproduct<M, float2>(sx, t);
+    cproduct<M, float2>(sa, t);
     if (live) {
         float2 *gx = reinterpret_cast<float2 *>(P.grad_x) + inst * Sh::N;
         float2 *ga = reinterpret_cast<float2 *>(P.grad_a) + inst * Sh::N;
@@ -360,6 +406,56 @@ int get_ctables(double fre, double fim, uint64_t n, const float2 **tw, const flo
     return FCIRC_OK;
 }
 
+// GF(p^2) twiddles per (f, n): s_{l,j} = rho^(2^(L-l-1)) psi_{2^(l+1)}^brv(j)
+// with rho a 2^L-th root of f and psi_m a primitive m-th root of unity
+// (gfp2.hpp), and their inverses; exact, cached per device.
+struct GPlanKey {
+    int dev;
+    uint32_t re, im;
+    uint64_t n;
+    bool operator<(const GPlanKey &o) const { return std::tie(dev, re, im, n) < std::tie(o.dev, o.re, o.im, o.n); }
+};
+std::map<GPlanKey, std::pair<uint2 *, uint2 *>> g_gplans;
+
+int get_gtables(uint32_t fre, uint32_t fim, uint64_t n, const uint2 **tw, const uint2 **itw)
+{
+    int dev = 0;
+    FCIRC_CUDA_TRY(cudaGetDevice(&dev));
+    const GPlanKey key{dev, fre, fim, n};
+    std::lock_guard<std::mutex> lk(g_cmu);
+    auto it = g_gplans.find(key);
+    if (it == g_gplans.end()) {
+        const int m = ilog2(n), L = m - 1;
+        gf::E rho;
+        if (!gf::root_2k(gf::E{fre, fim}, L, rho))
+            return fail(FCIRC_ENOROOT, "GF(p^2) product: f = %u + %u sqrt 3 has no 2^%d-th root", fre, fim, L);
+        std::vector<uint2> h(n / 2), hi(n / 2);
+        h[0] = hi[0] = make_uint2(0u, 0u);
+        for (int l = 0; l < L; ++l) {
+            const gf::E r = gf::pow(rho, (uint64_t)1 << (L - l - 1));
+            const gf::E psi = gf::root_of_unity(l + 1);
+            for (uint64_t j = 0; j < ((uint64_t)1 << l); ++j) {
+                const gf::E s = gf::mul(r, gf::pow(psi, host::bitrev(j, l)));
+                const gf::E si = gf::inv(s);
+                h[((size_t)1 << l) + j] = make_uint2(s.re, s.im);
+                hi[((size_t)1 << l) + j] = make_uint2(si.re, si.im);
+            }
+        }
+        uint2 *d = nullptr, *di = nullptr;
+        if (cudaMalloc(&d, n / 2 * sizeof(uint2)) != cudaSuccess || cudaMalloc(&di, n / 2 * sizeof(uint2)) != cudaSuccess) {
+            (void)cudaGetLastError();
+            cudaFree(d);
+            return fail(FCIRC_ENOMEM, "GF(p^2) plan: cudaMalloc failed");
+        }
+        FCIRC_CUDA_TRY(cudaMemcpy(d, h.data(), n / 2 * sizeof(uint2), cudaMemcpyHostToDevice));
+        FCIRC_CUDA_TRY(cudaMemcpy(di, hi.data(), n / 2 * sizeof(uint2), cudaMemcpyHostToDevice));
+        it = g_gplans.emplace(key, std::make_pair(d, di)).first;
+    }
+    *tw = it->second.first;
+    *itw = it->second.second;
+    return FCIRC_OK;
+}
+
 template <class K>
 int set_smem(K kernel, int bytes)
 {
@@ -376,6 +472,19 @@ int launch_cfwd_m(const CParams &P, cudaStream_t s)
     const uint64_t grid = (P.batch + Sh::IPC - 1) / Sh::IPC;
     ProfScope ps("k_cfwd", s);
     k_cfwd<M><<<(unsigned)grid, Sh::CT, smem, s>>>(P);
+    FCIRC_CUDA_TRY(cudaGetLastError());
+    return FCIRC_OK;
+}
+
+template <int M>
+int launch_gfwd_m(const GParams &P, cudaStream_t s)
+{
+    using Sh = CShape<M>;
+    const int smem = Sh::IPC * 2 * Sh::N * (int)sizeof(uint2);
+    FCIRC_TRY(set_smem(k_gfwd<M>, smem));
+    const uint64_t grid = (P.batch + Sh::IPC - 1) / Sh::IPC;
+    ProfScope ps("k_gfwd", s);
+    k_gfwd<M><<<(unsigned)grid, Sh::CT, smem, s>>>(P);
     FCIRC_CUDA_TRY(cudaGetLastError());
     return FCIRC_OK;
 }
@@ -405,6 +514,35 @@ void release_cplans()
         cudaFree(kv.second.second);
     }
     g_cplans.clear();
+    for (auto &kv : g_gplans) {
+        cudaSetDevice(kv.first.dev);
+        cudaDeviceSynchronize();
+        cudaFree(kv.second.first);
+        cudaFree(kv.second.second);
+    }
+    g_gplans.clear();
+}
+
+int gf_tables(uint32_t fre, uint32_t fim, uint64_t n, const uint2 **tw, const uint2 **itw)
+{
+    return get_gtables(fre, fim, n, tw, itw);
+}
+
+int launch_gfwd(const GParams &P, int m, cudaStream_t s)
+{
+    switch (m) {
+    case 3: return launch_gfwd_m<3>(P, s);
+    case 4: return launch_gfwd_m<4>(P, s);
+    case 5: return launch_gfwd_m<5>(P, s);
+    case 6: return launch_gfwd_m<6>(P, s);
+    case 7: return launch_gfwd_m<7>(P, s);
+    case 8: return launch_gfwd_m<8>(P, s);
+    case 9: return launch_gfwd_m<9>(P, s);
+    case 10: return launch_gfwd_m<10>(P, s);
+    case 11: return launch_gfwd_m<11>(P, s);
+    case 12: return launch_gfwd_m<12>(P, s);
+    default: return fail(FCIRC_EINVAL, "GF(p^2) product: n = 2^%d not supported", m);
+    }
 }
 
 int complex_tables(double fre, double fim, uint64_t n, const float2 **tw, const float2 **itw)

@@ -23,6 +23,18 @@ struct CBwdParams {
     float scale;
 };
 
+// GF(p^2), p = 2^31 - 1 (gfp2.hpp): elements as (re, im) uint32 pairs.
+struct GParams {
+    const uint32_t *a, *x;
+    uint32_t *c;
+    const uint2 *tw, *itw;
+    uint64_t batch;
+    uint32_t scale;   // 2^-L mod p
+};
+
+int gf_tables(uint32_t fre, uint32_t fim, uint64_t n, const uint2 **tw, const uint2 **itw);
+int launch_gfwd(const GParams &P, int m, cudaStream_t s);
+
 // Twiddles s_{l,j} of the product with parameter f and size n (FP64
 // rounded to FP32), cached per device.
 int complex_tables(double fre, double fim, uint64_t n, const float2 **tw, const float2 **itw);

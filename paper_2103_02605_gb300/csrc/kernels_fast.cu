@@ -317,7 +317,7 @@ __device__ __forceinline__ void colinv_stage(const ColInvParams &P, uint32_t *sm
                 const uint32_t row = row0 + (i << LST);
                 const int w = cphi(row, col);
                 const uint32_t idx = base + (row << logS) + col;
-                const uint32_t dst = (idx + mask) & mask;   // c_k = d_{k+1}
+                const uint32_t dst = (idx + mask) & mask;   // coefficient k is circulant entry k + 1
                 if (dst < P.nout) P.dst64[dst] = crt3(sm[w], sm[R * 4 + w], sm[2 * R * 4 + w], P.crt);
             }
         }

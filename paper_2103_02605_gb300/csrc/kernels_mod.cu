@@ -133,7 +133,7 @@ k_strided_inv(const __grid_constant__ StrInvParams P)
         for (int e = threadIdx.x; e < RW; e += blockDim.x) {
             const int r = e >> logW, w = e & (W - 1);
             const uint64_t idx = base + ((uint64_t)r << logS) + w;
-            const uint64_t dst = (idx + mask) & mask;   // c_k = d_{k+1}
+            const uint64_t dst = (idx + mask) & mask;   // coefficient k is circulant entry k + 1
             if (dst < P.nout) {
                 const uint32_t r1 = reduce_once(tile[e], P.job[0].p);
                 const uint32_t r2 = reduce_once(tile[RW + e], P.job[1].p);

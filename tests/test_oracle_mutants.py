@@ -45,6 +45,11 @@ MUTANTS = {
     # Toeplitz: diagonal index mirrored
     "toeplitz_mirror": ("acc = (acc + mulmod_u64(t[j + n - 1 - i], x[j], p)) % p;",
                         "acc = (acc + mulmod_u64(t[i + n - 1 - j], x[j], p)) % p;"),
+    # GF(p^2): 3 dropped from the sqrt 3 * sqrt 3 term
+    "gf_no_three": ("*cr = (ar * br % GFP + 3 * (ai * bi % GFP)) % GFP;",
+                    "*cr = (ar * br % GFP + (ai * bi % GFP)) % GFP;"),
+    # GF(p^2): f missing from the wrapped terms
+    "gf_drop_f": ("gf_mul(f_re, f_im, lr, li, &pr, &pi);", "pr = lr; pi = li;"),
     # off-by-one in the polynomial product window
     "poly_window": ("for (uint64_t i = lo; i <= hi; ++i)\n        s +=",
                     "for (uint64_t i = lo + 1; i <= hi; ++i)\n        s +="),
@@ -65,6 +70,8 @@ PIN_CALLS = [
     lambda o: pins.test_transpose_is_polynomial_product_mod_xn_minus_f(o, 8),
     lambda o: pins.test_column_convention_is_the_transpose(o, 8),
     lambda o: pins.test_toeplitz_oracle(o, 6),
+    lambda o: pins.test_gf_oracle_is_four_products_over_the_prime_field(o, 8),
+    lambda o: pins.test_gf_oracle_shift_and_identity_rows(o, 5),
     lambda o: pins.test_algorithm1_bruteforce_equals_dense(o, 16, None),
     lambda o: pins.test_complex_gradients_finite_differences(o, 0.6 + 0.8j),
     lambda o: pins.test_complex_gradients_finite_differences(o, 2.0 - 0.5j),

@@ -236,6 +236,49 @@ def test_toeplitz_oracle(orc, n):
     assert np.array_equal(orc.toeplitz_matvec_mod(P, tc, x), orc.fcirc_matvec_mod(P, f, a, x))
 
 
+# -- the paper's own field GF(p^2) = Z/pZ[sqrt 3], p = 2^31 - 1 ----------------
+
+GFP = (1 << 31) - 1
+
+
+def _gf_pairs(rng, n):
+    return rng.integers(0, GFP, (n, 2), dtype=np.uint64).astype(np.uint32)
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 8, 16])
+def test_gf_oracle_is_four_products_over_the_prime_field(orc, n):
+    """With f in Z/pZ the product splits: (A1 + s A2)(x1 + s x2) =
+    (A1 x1 + 3 A2 x2) + s (A1 x2 + A2 x1), s = sqrt 3, each term a product of
+    the modular oracle over p = 2^31 - 1 (linearity of Definition 2 in a)."""
+    rng = np.random.default_rng(600 + n)
+    a, x = _gf_pairs(rng, n), _gf_pairs(rng, n)
+    f = int(rng.integers(1, GFP))
+    got = orc.fcirc_matvec_gf((f, 0), a, x)
+    m = lambda u, v: orc.fcirc_matvec_mod(GFP, f, u, v).astype(np.uint64)
+    a1, a2, x1, x2 = a[:, 0], a[:, 1], x[:, 0], x[:, 1]
+    re = (m(a1, x1) + 3 * m(a2, x2)) % GFP
+    im = (m(a1, x2) + m(a2, x1)) % GFP
+    assert np.array_equal(got[:, 0], re.astype(np.uint32)) and np.array_equal(got[:, 1], im.astype(np.uint32))
+
+
+@pytest.mark.parametrize("n", [2, 5, 8])
+def test_gf_oracle_shift_and_identity_rows(orc, n):
+    """a = e_0 gives x; a = e_1 gives the f-shift c_i = x_{i+1}, c_{n-1} = f x_0
+    (f with a sqrt 3 part: the only place the field's product with f shows)."""
+    rng = np.random.default_rng(700 + n)
+    x = _gf_pairs(rng, n)
+    fr, fi = (int(v) for v in rng.integers(1, GFP, 2))
+    e0 = np.zeros((n, 2), np.uint32)
+    e0[0, 0] = 1
+    assert np.array_equal(orc.fcirc_matvec_gf((fr, fi), e0, x), x)
+    e1 = np.zeros((n, 2), np.uint32)
+    e1[1, 0] = 1
+    got = orc.fcirc_matvec_gf((fr, fi), e1, x)
+    assert np.array_equal(got[:-1], x[1:])
+    xr, xi = int(x[0, 0]), int(x[0, 1])
+    assert (int(got[-1, 0]), int(got[-1, 1])) == ((fr * xr + 3 * fi * xi) % GFP, (fr * xi + fi * xr) % GFP)
+
+
 # -- the paper's Algorithm 1 (brute force) agrees with the dense oracle ----------
 
 @pytest.mark.parametrize("n", [1, 2, 4, 8, 16, 32])
