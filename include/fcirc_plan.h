@@ -34,6 +34,12 @@ extern "C" {
  * = f.  FCIRC_ENOROOT if f = 0 or none exists, FCIRC_EINVAL for a bad p. */
 int fcirc_nth_root(uint32_t p, uint32_t f, uint32_t log2k, uint32_t *root);
 
+/* The same in the paper's field GF(p^2) = Z/pZ[sqrt 3], p = 2^31 - 1
+ * (Section 3.1): a 2^log2k-th root (r_re + r_im sqrt 3) of f_re + f_im sqrt 3,
+ * log2k <= 30.  FCIRC_ENOROOT if f = 0 or none exists, FCIRC_EINVAL for a
+ * non-canonical f or log2k > 30. */
+int fcirc_gf_nth_root(uint32_t f_re, uint32_t f_im, uint32_t log2k, uint32_t *r_re, uint32_t *r_im);
+
 /* The twiddle s_{l,j} (and its inverse) used at node j of level l of the
  * plan for (p, f, n); requires 0 <= l < log2(n) - 1 and j < 2^l. */
 int fcirc_node_twiddle(uint32_t p, uint32_t f, uint64_t n, uint32_t level,

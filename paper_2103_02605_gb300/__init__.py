@@ -68,6 +68,7 @@ _SIGNATURES = {
     "fcirc_last_error": ([], ctypes.c_char_p),
     "fcirc_release": ([], _i32),
     "fcirc_nth_root": ([_u32, _u32, _u32, ctypes.POINTER(_u32)], _i32),
+    "fcirc_gf_nth_root": ([_u32, _u32, _u32, ctypes.POINTER(_u32), ctypes.POINTER(_u32)], _i32),
     "fcirc_node_twiddle": ([_u32, _u32, _u64, _u32, _u64, ctypes.POINTER(_u32), ctypes.POINTER(_u32)], _i32),
     "fcirc_leaf_param": ([_u32, _u32, _u64, _u64, ctypes.POINTER(_u32)], _i32),
     "fcirc_twiddle_from_factor": ([_u32, _u32, _u32, ctypes.POINTER(_u32), ctypes.POINTER(_u32)], _i32),

@@ -33,6 +33,7 @@
 #include "../../include/fcirc_plan.h"
 #include "common.hpp"
 #include "kernels_mod.hpp"
+#include "gfp2.hpp"
 #include "ring.hpp"
 
 namespace fcirc {
@@ -475,6 +476,20 @@ int fcirc_nth_root(uint32_t p, uint32_t f, uint32_t log2k, uint32_t *root)
     if (!host::nth_root_2k(f, (int)log2k, p, r))
         return fail(FCIRC_ENOROOT, "f = %u has no 2^%u-th root mod %u", f, log2k, p);
     *root = r;
+    return FCIRC_OK;
+}
+
+int fcirc_gf_nth_root(uint32_t f_re, uint32_t f_im, uint32_t log2k, uint32_t *r_re, uint32_t *r_im)
+{
+    using namespace fcirc;
+    if (!r_re || !r_im) return fail(FCIRC_EINVAL, "null output");
+    if (f_re >= gf::P || f_im >= gf::P) return fail(FCIRC_EINVAL, "f not canonical mod 2^31 - 1");
+    if (log2k > 30) return fail(FCIRC_EINVAL, "log2k = %u too large", log2k);
+    gf::E r;
+    if (!gf::root_2k(gf::E{f_re, f_im}, (int)log2k, r))
+        return fail(FCIRC_ENOROOT, "%u + %u sqrt 3 has no 2^%u-th root", f_re, f_im, log2k);
+    *r_re = r.re;
+    *r_im = r.im;
     return FCIRC_OK;
 }
 

@@ -153,3 +153,51 @@ def test_twiddle_from_factor_matches_exact_division(F):
         for u, s in ((0, 0), (p - 1, p - 1), (1, p - 1), (p - 1, 1), (0, p - 1)):
             w, wp = F.twiddle_from_factor(p, u, s)
             assert (w, wp) == (u * s % p, ((u * s % p) << 32) // p)
+
+
+# -- the paper's field GF(p^2) = Z/pZ[sqrt 3], p = 2^31 - 1 -------------------------
+
+GFP = (1 << 31) - 1
+
+
+def _gmul(a, b):
+    return ((a[0] * b[0] + 3 * a[1] * b[1]) % GFP, (a[0] * b[1] + a[1] * b[0]) % GFP)
+
+
+def _gpow(a, e):
+    r = (1, 0)
+    while e:
+        if e & 1:
+            r = _gmul(r, a)
+        a = _gmul(a, a)
+        e >>= 1
+    return r
+
+
+def _gf_root(F, f, k):
+    import ctypes
+    rr, ri = ctypes.c_uint32(), ctypes.c_uint32()
+    st = F.load().fcirc_gf_nth_root(f[0], f[1], k, ctypes.byref(rr), ctypes.byref(ri))
+    return st, (rr.value, ri.value)
+
+
+def test_gf_roots(F):
+    """Roots in the paper's field: r^(2^k) = f for f that are 2^k-th powers;
+    3 is not a square mod p (so sqrt 3 extends Z/pZ); the element of order
+    2^32 has no square root; -1 has roots up to order 2^31 (p + 1 = 2^31)."""
+    assert pow(3, (GFP - 1) // 2, GFP) == GFP - 1
+    rng = np.random.default_rng(5)
+    for k in (0, 1, 5, 11, 30):
+        for _ in range(4):
+            b = tuple(int(v) for v in rng.integers(1, GFP, 2))
+            f = _gpow(b, 1 << k)
+            st, r = _gf_root(F, f, k)
+            assert st == 0 and _gpow(r, 1 << k) == f
+    st, r = _gf_root(F, (GFP - 1, 0), 30)
+    assert st == 0 and _gpow(r, 1 << 30) == (GFP - 1, 0)
+    # a generator g of the 2-Sylow subgroup: g^2 = 2 + sqrt 3 (the paper's generator)
+    st, g = _gf_root(F, (2, 1), 1)
+    assert st == 0 and _gpow(g, 1 << 31) == (GFP - 1, 0)
+    assert _gf_root(F, g, 1)[0] == 2
+    assert _gf_root(F, (0, 0), 3)[0] == 2
+    assert _gf_root(F, (GFP, 0), 3)[0] == 1
