@@ -153,6 +153,16 @@ __device__ __forceinline__ int tphi(int e)
     return (((r << 3) | (col ^ g)) << 2) | (e & 3);
 }
 
+// The three patterns as a per-thread base and terms that are compile-time
+// constants in the unrolled loops (so every access is one XOR at most and an
+// immediate offset; identities checked for every thread on the CPU):
+//   tphi(tid + 256 j)  = (tphi(tid) ^ 16 (j & 1)) + 256 j
+//   tphi(eb + 16 m)    = (tphi(eb) ^ (4 ((m >> 1) & 3) | 16 (m & 1))) + 32 (m >> 1)
+//   tphi(16 tid + 4 q) = tphi(16 tid) ^ 4 q
+__device__ __forceinline__ int tphiA(int tA, int j) { return (tA ^ ((j & 1) << 4)) + (j << 8); }
+__device__ __forceinline__ int tphiB(int tB, int m) { return (tB ^ ((((m >> 1) & 3) << 2) | ((m & 1) << 4))) + ((m >> 1) << 5); }
+__device__ __forceinline__ int tphiC(int tC, int q) { return tC ^ (q << 2); }
+
 // One tile: J gives the sides, destination, tables and prime; base is the
 // tile's first index in arrays of length N; sg its 11 levels of factors
 // (6 words each, see plan.cu); SA, SX (4096 words each, 16-byte aligned),
@@ -185,6 +195,7 @@ __device__ __forceinline__ void tile4096_dev(const TileJob &J, uint32_t N, uint3
     }
     __syncthreads();
 
+    const int tA = tphi(tid);
     // stage A: tile levels 0..3, residues tid + 256 j
     auto twA = [&](int d, int j) { return STW[(1 << d) + j]; };
     if (DO_A && DO_X)
@@ -195,16 +206,17 @@ __device__ __forceinline__ void tile4096_dev(const TileJob &J, uint32_t N, uint3
         fwd1<4, 4, true>(x, twA, p, p2);
 #pragma unroll
     for (int j = 0; j < 16; ++j) {
-        if (DO_A) SA[tphi(tid + 256 * j)] = a[j];
-        if (DO_X) SX[tphi(tid + 256 * j)] = x[j];
+        if (DO_A) SA[tphiA(tA, j)] = a[j];
+        if (DO_X) SX[tphiA(tA, j)] = x[j];
     }
     __syncthreads();
     // stage B: levels 4..7, residues 256 (tid >> 4) + 16 m + (tid & 15)
     const int eb = ((tid >> 4) << 8) + (tid & 15);
+    const int tB = tphi(eb), tC = tphi(16 * tid);
 #pragma unroll
     for (int m = 0; m < 16; ++m) {
-        if (DO_A) a[m] = SA[tphi(eb + 16 * m)];
-        if (DO_X) x[m] = SX[tphi(eb + 16 * m)];
+        if (DO_A) a[m] = SA[tphiB(tB, m)];
+        if (DO_X) x[m] = SX[tphiB(tB, m)];
     }
     const int nb = tid >> 4;
     auto twB = [&](int d, int j) { return STW[(1 << (4 + d)) + (nb << d) + j]; };
@@ -217,19 +229,19 @@ __device__ __forceinline__ void tile4096_dev(const TileJob &J, uint32_t N, uint3
     __syncthreads();
 #pragma unroll
     for (int m = 0; m < 16; ++m) {
-        if (DO_A) SA[tphi(eb + 16 * m)] = a[m];
-        if (DO_X) SX[tphi(eb + 16 * m)] = x[m];
+        if (DO_A) SA[tphiB(tB, m)] = a[m];
+        if (DO_X) SX[tphiB(tB, m)] = x[m];
     }
     __syncthreads();
     // stage C: levels 8..10 and the leaves, residues 16 tid .. 16 tid + 15
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
         if (DO_A) {
-            const uint4 va = *reinterpret_cast<const uint4 *>(&SA[tphi(16 * tid + 4 * q)]);
+            const uint4 va = *reinterpret_cast<const uint4 *>(&SA[tphiC(tC, q)]);
             a[4 * q] = va.x; a[4 * q + 1] = va.y; a[4 * q + 2] = va.z; a[4 * q + 3] = va.w;
         }
         if (DO_X) {
-            const uint4 vx = *reinterpret_cast<const uint4 *>(&SX[tphi(16 * tid + 4 * q)]);
+            const uint4 vx = *reinterpret_cast<const uint4 *>(&SX[tphiC(tC, q)]);
             x[4 * q] = vx.x; x[4 * q + 1] = vx.y; x[4 * q + 2] = vx.z; x[4 * q + 3] = vx.w;
         }
     }
@@ -282,18 +294,18 @@ __device__ __forceinline__ void tile4096_dev(const TileJob &J, uint32_t N, uint3
     __syncthreads();
 #pragma unroll
     for (int q = 0; q < 4; ++q)
-        *reinterpret_cast<uint4 *>(&SA[tphi(16 * tid + 4 * q)]) =
+        *reinterpret_cast<uint4 *>(&SA[tphiC(tC, q)]) =
             make_uint4(a[4 * q], a[4 * q + 1], a[4 * q + 2], a[4 * q + 3]);
     __syncthreads();
 #pragma unroll
-    for (int m = 0; m < 16; ++m) a[m] = SA[tphi(eb + 16 * m)];
+    for (int m = 0; m < 16; ++m) a[m] = SA[tphiB(tB, m)];
     rec1<4, 4>(a, [&](int d, int j) { return SITW[(1 << (4 + d)) + (nb << d) + j]; }, p, p2);
     __syncthreads();
 #pragma unroll
-    for (int m = 0; m < 16; ++m) SA[tphi(eb + 16 * m)] = a[m];
+    for (int m = 0; m < 16; ++m) SA[tphiB(tB, m)] = a[m];
     __syncthreads();
 #pragma unroll
-    for (int j = 0; j < 16; ++j) a[j] = SA[tphi(tid + 256 * j)];
+    for (int j = 0; j < 16; ++j) a[j] = SA[tphiA(tA, j)];
     rec1<4, 4>(a, [&](int d, int j) { return SITW[(1 << d) + j]; }, p, p2);
 #pragma unroll
     for (int j = 0; j < 16; ++j) J.dst[base + tid + 256 * j] = J.store_lazy ? a[j] : reduce_once(a[j], p);

@@ -134,3 +134,18 @@ def test_four_column_store_phase(LF, maxlcl, LR):
                     for groups in per_cta.values():
                         assert len(set(groups)) == len(groups)
     assert len(cover) == (1 << LCQ) << LF and set(cover.values()) == {1}
+
+
+def test_tile_address_identities():
+    """The tile kernel computes its shared-memory addresses from per-thread
+    bases and compile-time terms; the identities behind that, for every
+    thread and every unrolled index."""
+    for tid in range(256):
+        tA = tphi(tid)
+        eb = ((tid >> 4) << 8) + (tid & 15)
+        tB, tC = tphi(eb), tphi(16 * tid)
+        for j in range(16):
+            assert tphi(tid + 256 * j) == (tA ^ ((j & 1) << 4)) + (j << 8)
+            assert tphi(eb + 16 * j) == (tB ^ ((((j >> 1) & 3) << 2) | ((j & 1) << 4))) + ((j >> 1) << 5)
+        for q in range(4):
+            assert tphi(16 * tid + 4 * q) == tC ^ (q << 2)
