@@ -111,6 +111,45 @@ __device__ __forceinline__ int c4_off(int quad, int row)
     return (quad << (LF + 2)) + ((row ^ ((row >> kC4LR) & 7) ^ qs) << 2);
 }
 
+// The stage accesses c4_off(quad, row0 + i 2^LST) split into a per-group
+// base and terms that are compile-time constants in the unrolled loops (one
+// XOR at most and an immediate offset per access).  The stage shapes have
+// LST = 0, 4 or >= 7; the identities hold for every thread and group of
+// every shape (checked on the CPU).
+template <int LF, int LST>
+struct C4Addr {
+    static_assert(LST == 0 || LST == 4 || LST >= 7, "stage shape");
+    int rb, kt;
+    __device__ __forceinline__ C4Addr(int quad, int row0)
+    {
+        const int q = ((quad & 3) << 1) | ((quad >> 2) & 1);
+        if constexpr (kC4LR != 4) {
+            rb = quad;
+            kt = row0;
+        } else if constexpr (LST >= 7) {
+            rb = (quad << (LF + 2)) + ((row0 ^ ((row0 >> kC4LR) & 7) ^ q) << 2);
+            kt = 0;
+        } else if constexpr (LST == 4) {
+            rb = (quad << (LF + 2)) + ((row0 ^ q) << 2);
+            kt = 0;
+        } else {
+            rb = (quad << (LF + 2)) + (row0 << 2);
+            kt = ((row0 >> kC4LR) & 7) ^ q;
+        }
+    }
+    __device__ __forceinline__ int operator()(int i) const
+    {
+        if constexpr (kC4LR != 4)
+            return c4_off<LF>(rb, kt + (i << LST));
+        else if constexpr (LST >= 7)
+            return rb + (i << (LST + 2));
+        else if constexpr (LST == 4)
+            return (rb ^ ((i & 7) << 2)) + (i << 6);
+        else
+            return rb + ((i ^ kt) << 2);
+    }
+};
+
 // Barrier halves over the CTAs that share row segments (the cluster, or the
 // CTA itself when CL = 1).  Every thread alternates arrive and wait.
 template <int CL>
@@ -325,7 +364,7 @@ __device__ __forceinline__ void c4fwd_stage(const ColFwdJob &J, const ColFwdPara
             if constexpr (FIRST)
                 w = ld4_raw<MODE>(J.src, P.N, base + ((uint32_t)quad << 2) + ((uint32_t)row << logS));
             else
-                w = *reinterpret_cast<const uint4 *>(sm + c4_off<LF>(quad, row));
+                w = *reinterpret_cast<const uint4 *>(sm + C4Addr<LF, LST>(quad, row0)(i));
             put4(v + 4 * (hb * M + i), w);
         }
     }
@@ -371,11 +410,9 @@ __device__ __forceinline__ void c4fwd_stage(const ColFwdJob &J, const ColFwdPara
     for (int hb = 0; hb < B; ++hb) {
         int quad, row0, blk;
         c4_group<LF, D0, NL>(tid, hb, quad, row0, blk);
+        const C4Addr<LF, LST> ad(quad, row0);
 #pragma unroll
-        for (int i = 0; i < M; ++i) {
-            const int row = row0 + (i << LST);
-            *reinterpret_cast<uint4 *>(sm + c4_off<LF>(quad, row)) = get4(v + 4 * (hb * M + i));
-        }
+        for (int i = 0; i < M; ++i) *reinterpret_cast<uint4 *>(sm + ad(i)) = get4(v + 4 * (hb * M + i));
     }
 }
 
@@ -463,7 +500,7 @@ __device__ __forceinline__ void c4inv_job(const ColInvParams &P, const ColInvJob
                     w = __ldg(reinterpret_cast<const uint4 *>(J.src + base + ((uint32_t)quad << 2) +
                                                               ((uint32_t)row << logS)));
                 else
-                    w = *reinterpret_cast<const uint4 *>(smq + c4_off<LF>(quad, row));
+                    w = *reinterpret_cast<const uint4 *>(smq + C4Addr<LF, LST>(quad, row0)(i));
                 put4(v + 4 * (hb * M + i), w);
             }
         }
@@ -482,14 +519,14 @@ __device__ __forceinline__ void c4inv_job(const ColInvParams &P, const ColInvJob
         for (int hb = 0; hb < B; ++hb) {
             int quad, row0, blk;
             c4_group<LF, D0, NL>(tid, hb, quad, row0, blk);
+            const C4Addr<LF, LST> ad(quad, row0);
 #pragma unroll
             for (int i = 0; i < M; ++i) {
-                const int row = row0 + (i << LST);
                 uint32_t *e = v + 4 * (hb * M + i);
                 const uint4 w = canon ? make_uint4(reduce_once(e[0], p), reduce_once(e[1], p),
                                                    reduce_once(e[2], p), reduce_once(e[3], p))
                                       : get4(e);
-                *reinterpret_cast<uint4 *>(smq + c4_off<LF>(quad, row)) = w;
+                *reinterpret_cast<uint4 *>(smq + ad(i)) = w;
             }
         }
     }

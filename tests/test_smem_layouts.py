@@ -149,3 +149,34 @@ def test_tile_address_identities():
             assert tphi(eb + 16 * j) == (tB ^ ((((j >> 1) & 3) << 2) | ((j & 1) << 4))) + ((j >> 1) << 5)
         for q in range(4):
             assert tphi(16 * tid + 4 * q) == tC ^ (q << 2)
+
+
+@pytest.mark.parametrize("LF", [8, 9, 10, 11, 12])
+def test_four_column_address_identities(LF):
+    """k_colfwd4 / k_colinv4 compute c4_off(quad, row0 + i 2^LST) as a
+    per-group base plus compile-time terms; the identities behind that for
+    every thread, group and row of every stage shape (2^4 rows per thread)."""
+    LR = 4
+    qs = lambda q: ((q & 3) << 1) | ((q >> 2) & 1)
+    NST = (LF + LR - 1) // LR
+    NL0 = LF - LR * (NST - 1)
+    for S in range(NST):
+        NL = NL0 if S == 0 else LR
+        D0 = 0 if S == 0 else NL0 + LR * (S - 1)
+        M, B, LST, LRB, LGQ = 1 << NL, 16 >> NL, LF - D0 - NL, LF - D0, LF - NL
+        assert LST in (0, 4) or LST >= 7
+        for t in range(256):
+            for h in range(B):
+                gg = t + 256 * h
+                quad, g = gg >> LGQ, gg & ((1 << LGQ) - 1)
+                row0 = ((g >> LST) << LRB) + (g & ((1 << LST) - 1))
+                for i in range(M):
+                    want = 4 * c4_off16(LF, quad, row0 + (i << LST), LR)
+                    if LST >= 7:
+                        got = (quad << (LF + 2)) + ((row0 ^ ((row0 >> 4) & 7) ^ qs(quad)) << 2) + (i << (LST + 2))
+                    elif LST == 4:
+                        got = (((quad << (LF + 2)) + ((row0 ^ qs(quad)) << 2)) ^ ((i & 7) << 2)) + (i << 6)
+                    else:
+                        kt = ((row0 >> 4) & 7) ^ qs(quad)
+                        got = (quad << (LF + 2)) + (row0 << 2) + ((i ^ kt) << 2)
+                    assert got == want
