@@ -257,7 +257,7 @@ _KSRC = {
     "k_tile4096": ["kernels_tile.cu", "tile_dev.cuh", "modarith.cuh", "kernels_mod.hpp"],
 }
 NCU_TRAFFIC = {
-    "k_tile4096": (568101120, "007434b1fe6d99c2"),
+    "k_tile4096": (563590656, "58676623955ca72c"),
 }
 
 

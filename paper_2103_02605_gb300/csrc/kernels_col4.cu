@@ -56,8 +56,11 @@ constexpr int kC4Threads = 4096 >> kC4LR;
 #ifndef FCIRC_C4_MAXLCL
 #define FCIRC_C4_MAXLCL 1
 #endif
+// Whether the jobs of one group (the three primes of one side of a
+// polynomial product) get one CTA each; sharing a CTA reads their common
+// source from DRAM once instead of three times (64 vs 34 MB) at the same time.
 #ifndef FCIRC_C4_SPLITJOBS
-#define FCIRC_C4_SPLITJOBS 1
+#define FCIRC_C4_SPLITJOBS 0
 #endif
 #ifndef FCIRC_C4_X3
 #define FCIRC_C4_X3 1
@@ -692,8 +695,7 @@ int launch_c4fwd_m(const ColFwdParams &P, int nctay, cudaStream_t s)
     const int smem = C4<LF>::WORDS * 4;
     FCIRC_TRY(c4_smem(k_colfwd4<LF, M0, M1>, smem, mask));
     const uint64_t ncta = (uint64_t)1 << (P.l0 + (P.logn - P.l1) - 2 - C4<LF>::LNQ);
-    // one job per CTA: more, shorter CTAs (the jobs of one group share only
-    // their source, which the L2 serves)
+    // optionally one job per CTA (more, shorter CTAs)
     ColFwdParams P1 = P;
     int ny = nctay;
     if (FCIRC_C4_SPLITJOBS) {
