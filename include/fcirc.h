@@ -354,6 +354,27 @@ const char *fcirc_last_error(void);
  * time outside stream capture; later calls rebuild what they need. */
 int fcirc_release(void);
 
+/*
+ * fcirc_set_checks -- input checks on (1) or off (0; the default unless the
+ * environment variable FCIRC_CHECKS is set to a non-zero value when the
+ * library first needs it).  With checks on, every entry point that takes
+ * residues launches a kernel that compares them with p (2^31 - 1 for the
+ * GF(p^2) product) before the product runs; a value out of range sets the
+ * sticky device status word to FCIRC_EINVAL, which fcirc_sync_status then
+ * returns.  Nothing traps and the product still runs (its result for such
+ * inputs is unspecified, never out of bounds).  Always FCIRC_OK.
+ */
+int fcirc_set_checks(int on);
+
+/*
+ * fcirc_debug_fail_alloc -- fault injection for tests: the k-th next device
+ * allocation the library makes (k = 0: the next one) fails as if the device
+ * were out of memory, so the entry point that asked returns FCIRC_ENOMEM
+ * with the library's caches left consistent.  k < 0 switches it off.  Always
+ * FCIRC_OK.
+ */
+int fcirc_debug_fail_alloc(int k);
+
 #ifdef __cplusplus
 }
 #endif

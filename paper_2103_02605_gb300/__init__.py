@@ -28,7 +28,7 @@ __all__ = [
     "FcircError", "library_path", "load",
     "fcirc_matvec", "fcirc_matvec_t", "fcirc_toeplitz_matvec", "fcirc_matvec_gf", "GF_P", "fcirc_matvec_noalloc", "APlan", "poly_mul_int", "bigint_mul",
     "fcirc_matvec_c64", "fcirc_matvec_backward", "fcirc_layer",
-    "fcirc_matvec_batched", "batched_autotune", "BatchedGraph", "sync_status", "release",
+    "fcirc_matvec_batched", "batched_autotune", "BatchedGraph", "sync_status", "release", "set_checks",
     "nth_root", "node_twiddle", "leaf_param", "twiddle_from_factor",
     "prof_start", "prof_stop", "prof_report", "prof_launches",
     "PRIMES",
@@ -67,6 +67,8 @@ _SIGNATURES = {
     "fcirc_error_string": ([_i32], ctypes.c_char_p),
     "fcirc_last_error": ([], ctypes.c_char_p),
     "fcirc_release": ([], _i32),
+    "fcirc_set_checks": ([_i32], _i32),
+    "fcirc_debug_fail_alloc": ([_i32], _i32),
     "fcirc_nth_root": ([_u32, _u32, _u32, ctypes.POINTER(_u32)], _i32),
     "fcirc_gf_nth_root": ([_u32, _u32, _u32, ctypes.POINTER(_u32), ctypes.POINTER(_u32)], _i32),
     "fcirc_node_twiddle": ([_u32, _u32, _u64, _u32, _u64, ctypes.POINTER(_u32), ctypes.POINTER(_u32)], _i32),
@@ -462,6 +464,12 @@ def sync_status(stream=None) -> int:
     st = int(getattr(stream, "cuda_stream", stream)) if stream is not None else (
         int(torch.cuda.current_stream().cuda_stream) if torch.cuda.is_available() else 0)
     return int(load().fcirc_sync_status(st))
+
+
+def set_checks(on: bool = True):
+    """Input range checks before every product (include/fcirc.h,
+    fcirc_set_checks); a violation shows up in sync_status()."""
+    _check(load().fcirc_set_checks(1 if on else 0), "fcirc_set_checks")
 
 
 def release():

@@ -305,6 +305,8 @@ static int embedded_matvec(uint32_t p, uint32_t f, const uint32_t *a, const uint
     st.args = {&aa, &ax, &ac};
     FCIRC_TRY(st.begin(s, 4 * N * 4));
     const uint32_t *da = static_cast<const uint32_t *>(aa.d), *dx = static_cast<const uint32_t *>(ax.d);
+    FCIRC_TRY(check_lt(da, na, p, s));
+    FCIRC_TRY(check_lt(dx, n, p, s));
     uint32_t *ap = reinterpret_cast<uint32_t *>(st.scratch), *bp = ap + N, *cp = bp + N, *xs = cp + N;
     const uint32_t fr = f % p;
     FCIRC_TRY(launch_embed(toeplitz ? da + (n - 1) : da, da, dx, n, N, Tw{fr, host::shoup_quot(fr, p)}, p,
@@ -431,6 +433,8 @@ int fcirc_matvec(uint32_t p, uint32_t f, const uint32_t *a, const uint32_t *x, u
         FCIRC_TRY(launch_scalar(da, dx, dc, p, s));
         return st.end();
     }
+    FCIRC_TRY(check_lt(da, n, p, s));
+    FCIRC_TRY(check_lt(dx, n, p, s));
     // the row vector is scaled by 2^32 2^-L on its first load (see leaf2)
     const Src sa{da, n, SRC_U32, 1, pl->kt};
     FCIRC_TRY(matvec_core(pl, sa, src_u32(dx, n), dc, reinterpret_cast<uint32_t *>(st.scratch), s));
@@ -472,6 +476,8 @@ int fcirc_matvec_t(uint32_t p, uint32_t f, const uint32_t *a, const uint32_t *x,
         FCIRC_TRY(launch_scalar(da, dx, dc, p, s));
         return st.end();
     }
+    FCIRC_TRY(check_lt(da, n, p, s));
+    FCIRC_TRY(check_lt(dx, n, p, s));
     uint32_t *cr = reinterpret_cast<uint32_t *>(st.scratch), *xs = cr + n;
     const Src sa{da, n, SRC_U32_REV, 1, pl->kt};
     FCIRC_TRY(matvec_core(pl, sa, src_u32(dx, n), cr, xs, s));
@@ -515,7 +521,7 @@ int fcirc_aplan_create(uint32_t p, uint32_t f, const uint32_t *a, uint64_t n, vo
     int dev = 0;
     FCIRC_CUDA_TRY(cudaGetDevice(&dev));
     void *mem = nullptr;
-    if (cudaMalloc(&mem, n * 4) != cudaSuccess) {
+    if (dev_alloc(&mem, n * 4) != cudaSuccess) {
         (void)cudaGetLastError();
         return fail(FCIRC_ENOMEM, "fcirc_aplan_create: %llu bytes of device memory", (unsigned long long)(n * 4));
     }
@@ -531,6 +537,8 @@ int fcirc_aplan_create(uint32_t p, uint32_t f, const uint32_t *a, uint64_t n, vo
     int rc = st.begin(s, 0);
     if (rc != FCIRC_OK) return undo(rc);
     const uint32_t *da = static_cast<const uint32_t *>(aa.d);
+    rc = check_lt(da, n, p, s);
+    if (rc != FCIRC_OK) return undo(rc);
     h->planned = pl && pl->logT == 12;
     if (!h->planned) {
         if (cudaMemcpyAsync(h->ahat, da, n * 4, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
@@ -578,6 +586,7 @@ int fcirc_matvec_aplan(fcirc_aplan_t h, const uint32_t *x, uint32_t *c, void *st
     FCIRC_TRY(st.begin(s, pl->k > 0 ? n * 4 : 0));
     const uint32_t *dx = static_cast<const uint32_t *>(ax.d);
     uint32_t *dc = static_cast<uint32_t *>(ac.d);
+    FCIRC_TRY(check_lt(dx, n, h->p, s));
     const Src sx = src_u32(dx, n), sah = src_u32(h->ahat, n);
     if (pl->k == 0) {
         TileParams tp;
@@ -737,6 +746,8 @@ int fcirc_matvec_gf(const uint32_t *a, const uint32_t *x, uint32_t *c, uint32_t 
     P.c = static_cast<uint32_t *>(ac.d);
     P.batch = batch;
     P.scale = gf::inv(gf::E{(uint32_t)1u << (m - 1), 0u}).re;   // 2^-L, L = m - 1
+    FCIRC_TRY(check_lt(P.a, 2 * n * batch, gf::P, s));
+    FCIRC_TRY(check_lt(P.x, 2 * n * batch, gf::P, s));
     FCIRC_TRY(launch_gfwd(P, m, s));
     return st.end();
 }
@@ -916,6 +927,8 @@ int fcirc_matvec_batched(uint32_t p, const uint32_t *f, const uint64_t *offsets,
     P.a = static_cast<const uint32_t *>(aa.d);
     P.x = static_cast<const uint32_t *>(ax.d);
     P.c = static_cast<uint32_t *>(ac.d);
+    FCIRC_TRY(check_lt(P.a, total, p, s));
+    FCIRC_TRY(check_lt(P.x, total, p, s));
     batch_carve(st.scratch, count, total, P);
     FCIRC_TRY(launch_with_config(P, tuned_config(p, count, total), s));
     return st.end();
@@ -1004,7 +1017,7 @@ int fcirc_matvec_batched_graph(uint32_t p, const uint32_t *f, const uint64_t *of
     BatchGraph *g = new BatchGraph();
     FCIRC_CUDA_TRY(cudaGetDevice(&g->dev));
     const size_t bytes = batch_scratch_bytes(count, total_n);
-    if (cudaMalloc(&g->scratch, bytes) != cudaSuccess) {
+    if (dev_alloc(&g->scratch, bytes) != cudaSuccess) {
         (void)cudaGetLastError();
         delete g;
         return fail(FCIRC_ENOMEM, "fcirc_matvec_batched_graph: cudaMalloc(%zu)", bytes);
@@ -1084,6 +1097,20 @@ int fcirc_sync_status(void *stream)
             return fail((int)v, "a batched instance was invalid or had no root (device status %u)", v);
         return fail(FCIRC_ETIMEOUT, "a bounded device-side wait gave up (code %u)", v);
     }
+    return FCIRC_OK;
+}
+
+int fcirc_set_checks(int on)
+{
+    set_error("");
+    set_checks(on != 0);
+    return FCIRC_OK;
+}
+
+int fcirc_debug_fail_alloc(int k)
+{
+    set_error("");
+    debug_fail_alloc(k);
     return FCIRC_OK;
 }
 

@@ -48,6 +48,18 @@ int scratch_acquire(cudaStream_t s, size_t bytes, void **out);
 // memory, 0 = OK), written by kernels whose bounded waits give up.
 int device_status_word(uint32_t **out);
 
+// Every device allocation of the library goes through dev_alloc, so that a
+// test can make one of them fail (fcirc_debug_fail_alloc).
+cudaError_t dev_alloc(void **ptr, size_t bytes);
+void debug_fail_alloc(int k);
+
+// Input checks (fcirc_set_checks): when on, check_lt launches a kernel that
+// sets the device status word to FCIRC_EINVAL if any of the n words at v is
+// >= bound; a no-op when off.
+bool checks_on();
+int check_lt(const uint32_t *v, uint64_t n, uint32_t bound, cudaStream_t s);
+void set_checks(bool on);
+
 // ---------------------------------------------------------------------------
 // Plans.
 

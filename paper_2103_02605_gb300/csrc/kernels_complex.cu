@@ -392,7 +392,8 @@ int get_ctables(double fre, double fim, uint64_t n, const float2 **tw, const flo
             }
         }
         float2 *d = nullptr, *di = nullptr;
-        if (cudaMalloc(&d, n / 2 * sizeof(float2)) != cudaSuccess || cudaMalloc(&di, n / 2 * sizeof(float2)) != cudaSuccess) {
+        if (dev_alloc((void **)&d, n / 2 * sizeof(float2)) != cudaSuccess ||
+            dev_alloc((void **)&di, n / 2 * sizeof(float2)) != cudaSuccess) {
             (void)cudaGetLastError();
             cudaFree(d);
             return fail(FCIRC_ENOMEM, "complex plan: cudaMalloc failed");
@@ -442,7 +443,8 @@ int get_gtables(uint32_t fre, uint32_t fim, uint64_t n, const uint2 **tw, const 
             }
         }
         uint2 *d = nullptr, *di = nullptr;
-        if (cudaMalloc(&d, n / 2 * sizeof(uint2)) != cudaSuccess || cudaMalloc(&di, n / 2 * sizeof(uint2)) != cudaSuccess) {
+        if (dev_alloc((void **)&d, n / 2 * sizeof(uint2)) != cudaSuccess ||
+            dev_alloc((void **)&di, n / 2 * sizeof(uint2)) != cudaSuccess) {
             (void)cudaGetLastError();
             cudaFree(d);
             return fail(FCIRC_ENOMEM, "GF(p^2) plan: cudaMalloc failed");

@@ -21,6 +21,7 @@
 // is ever read.
 #include <atomic>
 
+#include <cstdlib>
 #include "common.hpp"
 #include "kernels_mod.hpp"
 #include "prof.hpp"
@@ -289,6 +290,47 @@ int launch_rot_scale(const uint32_t *src, uint32_t *dst, uint64_t n, Tw f, uint3
     if (blocks > 152 * 8) blocks = 152 * 8;
     ProfScope ps("k_rot_scale", s);
     k_rot_scale<<<blocks, 256, 0, s>>>(src, dst, n, f, p);
+    FCIRC_CUDA_TRY(cudaGetLastError());
+    return FCIRC_OK;
+}
+
+// Input check (fcirc_set_checks): any word >= bound sets the status word.
+__global__ void k_check_lt(const uint32_t *v, uint64_t n, uint32_t bound, uint32_t *status)
+{
+    bool bad = false;
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x)
+        bad = bad || v[i] >= bound;
+    if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicCAS(status, 0u, (uint32_t)FCIRC_EINVAL);
+}
+
+namespace {
+std::atomic<int> g_checks{-1};   // -1: not yet read from the environment
+}
+
+bool checks_on()
+{
+    int c = g_checks.load();
+    if (c < 0) {
+        const char *e = std::getenv("FCIRC_CHECKS");
+        c = (e && e[0] && e[0] != '0') ? 1 : 0;
+        int expect = -1;
+        g_checks.compare_exchange_strong(expect, c);
+        c = g_checks.load();
+    }
+    return c == 1;
+}
+
+void set_checks(bool on) { g_checks.store(on ? 1 : 0); }
+
+int check_lt(const uint32_t *v, uint64_t n, uint32_t bound, cudaStream_t s)
+{
+    if (!checks_on() || n == 0) return FCIRC_OK;
+    uint32_t *status;
+    FCIRC_TRY(device_status_word(&status));
+    unsigned blocks = (unsigned)((n + 255) / 256);
+    if (blocks > 152 * 4) blocks = 152 * 4;
+    ProfScope ps("k_check_lt", s);
+    k_check_lt<<<blocks, 256, 0, s>>>(v, n, bound, status);
     FCIRC_CUDA_TRY(cudaGetLastError());
     return FCIRC_OK;
 }

@@ -25,6 +25,7 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <atomic>
 #include <map>
 #include <mutex>
 #include <tuple>
@@ -75,6 +76,27 @@ std::map<std::pair<int, cudaStream_t>, ScratchBuf> g_scratch;
 std::map<int, uint32_t *> g_status;
 }  // namespace
 
+namespace {
+std::atomic<int> g_fail_alloc{-1};
+}
+
+void debug_fail_alloc(int k) { g_fail_alloc.store(k < 0 ? -1 : k); }
+
+cudaError_t dev_alloc(void **ptr, size_t bytes)
+{
+    int k = g_fail_alloc.load();
+    while (k >= 0) {
+        if (g_fail_alloc.compare_exchange_weak(k, k - 1)) {
+            if (k == 0) {
+                *ptr = nullptr;
+                return cudaErrorMemoryAllocation;
+            }
+            break;
+        }
+    }
+    return cudaMalloc(ptr, bytes);
+}
+
 int scratch_acquire(cudaStream_t s, size_t bytes, void **out)
 {
     int dev = 0;
@@ -90,7 +112,7 @@ int scratch_acquire(cudaStream_t s, size_t bytes, void **out)
         }
         size_t want = bytes + (bytes >> 3);
         want = (want + 0xFFFFF) & ~(size_t)0xFFFFF;
-        cudaError_t e = cudaMalloc(&b.ptr, want);
+        cudaError_t e = dev_alloc(&b.ptr, want);
         if (e != cudaSuccess) {
             (void)cudaGetLastError();
             b.ptr = nullptr;
@@ -148,9 +170,10 @@ static int upload(void **dptr, const void *src, size_t bytes)
         *dptr = nullptr;
         return FCIRC_OK;
     }
-    cudaError_t e = cudaMalloc(dptr, bytes);
+    cudaError_t e = dev_alloc(dptr, bytes);
     if (e != cudaSuccess) {
         (void)cudaGetLastError();
+        *dptr = nullptr;
         return fail(FCIRC_ENOMEM, "plan: cudaMalloc(%zu): %s", bytes, cudaGetErrorString(e));
     }
     FCIRC_CUDA_TRY(cudaMemcpy(*dptr, src, bytes, cudaMemcpyHostToDevice));
@@ -208,6 +231,8 @@ int prime_tables(uint32_t p, const PrimeTables **out)
     int s = upload((void **)&t->d_U, U.data(), U.size() * 4);
     if (s == FCIRC_OK) s = upload((void **)&t->d_Ui, Ui.data(), Ui.size() * 4);
     if (s != FCIRC_OK) {
+        cudaFree(t->d_U);
+        cudaFree(t->d_Ui);
         delete t;
         return s;
     }

@@ -1,4 +1,6 @@
-// prof.cu -- per-launch CUDA-event tracing (include/fcirc_prof.h).
+// prof.cu -- per-launch CUDA-event tracing (include/fcirc_prof.h), and an
+// NVTX range named after the kernel around every launch (visible to
+// profilers that collect NVTX; a no-op otherwise).
 #include <stdio.h>
 #include <string.h>
 
@@ -7,6 +9,8 @@
 #include <mutex>
 #include <string>
 #include <vector>
+
+#include <nvtx3/nvToolsExt.h>
 
 #include "../../include/fcirc_prof.h"
 #include "common.hpp"
@@ -46,6 +50,7 @@ bool prof_on() { return g_on.load(std::memory_order_relaxed); }
 
 ProfScope::ProfScope(const char *name, cudaStream_t s) : name_(name), s_(s)
 {
+    nvtxRangePushA(name);
     if (!prof_on()) return;
     int dev = 0;
     cudaGetDevice(&dev);
@@ -58,10 +63,12 @@ ProfScope::ProfScope(const char *name, cudaStream_t s) : name_(name), s_(s)
 
 ProfScope::~ProfScope()
 {
-    if (!e0_ || !e1_) return;
-    cudaEventRecord(e1_, s_);
-    std::lock_guard<std::mutex> lk(g_mu);
-    g_recs.push_back(Rec{name_, dev_, e0_, e1_});
+    if (e0_ && e1_) {
+        cudaEventRecord(e1_, s_);
+        std::lock_guard<std::mutex> lk(g_mu);
+        g_recs.push_back(Rec{name_, dev_, e0_, e1_});
+    }
+    nvtxRangePop();
 }
 
 }  // namespace fcirc
