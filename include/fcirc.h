@@ -317,6 +317,28 @@ int fcirc_matvec_gf(const uint32_t *a, const uint32_t *x, uint32_t *c, uint32_t 
                     uint64_t n, uint64_t batch, void *stream);
 
 /*
+ * fcirc_matvec_ssa -- a batch of f-circulant products over the ring
+ * Z/(2^K + 1), the ring of Schoenhage-Strassen multiplication (the
+ * conclusion of the paper proposes Algorithm 1 there).  2 has order 2K in
+ * that ring, so every root Algorithm 1 needs is a power of two and every
+ * twiddle product is a shift; only the leaf products multiply elements.
+ *
+ *   K        64 or 128.
+ *   a, x, c  batch instances of n elements; an element is K/64 + 1 uint64
+ *            words: K/64 little-endian words w and a top word t in {0, 1},
+ *            the value w + t 2^K in [0, 2^K] (t = 1 only with w = 0).
+ *            Results come back in the same form.
+ *   f        2^f_exp, 0 <= f_exp < 2K; Theorem 1's root must be a power of
+ *            two, i.e. 2^(log2 n - 1) divides f_exp (f_exp = 0: ordinary
+ *            circulants; f_exp = K: f = -1, negacyclic).
+ *   n        a power of two, 8 <= n <= min(512, 4K);  batch >= 0.
+ * Errors: FCIRC_EINVAL for null pointers, an unsupported K or n, or
+ * f_exp >= 2K; FCIRC_ENOROOT when 2^(log2 n - 1) does not divide f_exp.
+ */
+int fcirc_matvec_ssa(const uint64_t *a, const uint64_t *x, uint64_t *c, uint32_t K, uint32_t f_exp,
+                     uint64_t n, uint64_t batch, void *stream);
+
+/*
  * fcirc_matvec_backward -- gradients of the real loss L = Re <g, A x> (the
  * convention PyTorch uses for complex tensors: the gradient of z is
  * dL/dRe z + i dL/dIm z), for the same batch layout as fcirc_matvec_c64:

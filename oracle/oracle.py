@@ -132,6 +132,22 @@ def fcirc_matvec_gf(f, a, x) -> np.ndarray:
     return out.reshape(a.shape)
 
 
+def fcirc_matvec_ssa(K: int, f_exp: int, a, x) -> list:
+    """Over Z/(2^K + 1) with f = 2^f_exp: c_i = sum_k a_k x_{(i+k) mod n}
+    f^[i+k >= n] (Definition 2) in Python integers, for small n."""
+    M = (1 << K) + 1
+    f = pow(2, f_exp, M)
+    n = len(a)
+    out = []
+    for i in range(n):
+        s = 0
+        for k in range(n):
+            t = a[k] * x[(i + k) % n]
+            s += t * f if i + k >= n else t
+        out.append(s % M)
+    return out
+
+
 def fcirc_matvec_mod_rows(p: int, f: int, a, x, rows) -> np.ndarray:
     a, x = _u32(a), _u32(x)
     rows = np.ascontiguousarray(rows, dtype=np.uint64)

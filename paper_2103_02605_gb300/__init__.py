@@ -26,7 +26,7 @@ from . import build as _build
 
 __all__ = [
     "FcircError", "library_path", "load",
-    "fcirc_matvec", "fcirc_matvec_t", "fcirc_toeplitz_matvec", "fcirc_matvec_gf", "GF_P", "fcirc_matvec_noalloc", "APlan", "poly_mul_int", "bigint_mul",
+    "fcirc_matvec", "fcirc_matvec_t", "fcirc_toeplitz_matvec", "fcirc_matvec_gf", "GF_P", "fcirc_matvec_ssa", "fcirc_matvec_noalloc", "APlan", "poly_mul_int", "bigint_mul",
     "fcirc_matvec_c64", "fcirc_matvec_backward", "fcirc_layer",
     "fcirc_matvec_batched", "batched_autotune", "BatchedGraph", "sync_status", "release", "set_checks",
     "nth_root", "node_twiddle", "leaf_param", "twiddle_from_factor",
@@ -49,6 +49,7 @@ _SIGNATURES = {
     "fcirc_matvec_t": ([_u32, _u32, _vp, _vp, _vp, _u64, _vp], _i32),
     "fcirc_toeplitz_matvec": ([_u32, _vp, _vp, _vp, _u64, _vp], _i32),
     "fcirc_matvec_gf": ([_vp, _vp, _vp, _u32, _u32, _u64, _u64, _vp], _i32),
+    "fcirc_matvec_ssa": ([_vp, _vp, _vp, _u32, _u32, _u64, _u64, _vp], _i32),
     "fcirc_aplan_create": ([_u32, _u32, _vp, _u64, _vp, ctypes.POINTER(_vp)], _i32),
     "fcirc_matvec_aplan": ([_vp, _vp, _vp, _vp], _i32),
     "fcirc_aplan_destroy": ([_vp], _i32),
@@ -211,6 +212,28 @@ def fcirc_matvec_gf(a, x, f=(1, 0), out=None, stream=None):
     st = _stream_handle(stream, a, x, out)
     _check(load().fcirc_matvec_gf(a.data_ptr(), x.data_ptr(), out.data_ptr(), int(f[0]) % GF_P, int(f[1]) % GF_P,
                                   n, batch, st), "fcirc_matvec_gf")
+    return out
+
+
+def fcirc_matvec_ssa(a, x, K: int, f_exp: int = 0, out=None, stream=None):
+    """Batched f-circulant products over Z/(2^K + 1), f = 2^f_exp, K = 64 or
+    128 (include/fcirc.h).  a, x: int64/uint64 tensors of shape
+    (batch, n, K/64 + 1): K/64 little-endian words and a top word (value
+    w + top 2^K, at most 2^K)."""
+    import torch
+    wpe = K // 64 + 1
+    for t, nm in ((a, "a"), (x, "x")):
+        if t.dtype not in (torch.int64, getattr(torch, "uint64", torch.int64)):
+            raise TypeError(f"{nm} must be a 64-bit integer tensor")
+        if t.dim() != 3 or t.shape[2] != wpe or not t.is_contiguous():
+            raise ValueError(f"{nm} must be contiguous of shape (batch, n, {wpe})")
+    if a.shape != x.shape:
+        raise ValueError("a and x must have the same shape")
+    if out is None:
+        out = torch.empty_like(a)
+    st = _stream_handle(stream, a, x, out)
+    _check(load().fcirc_matvec_ssa(a.data_ptr(), x.data_ptr(), out.data_ptr(), K, f_exp, a.shape[1], a.shape[0], st),
+           "fcirc_matvec_ssa")
     return out
 
 

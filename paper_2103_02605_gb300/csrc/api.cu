@@ -752,6 +752,35 @@ int fcirc_matvec_gf(const uint32_t *a, const uint32_t *x, uint32_t *c, uint32_t 
     return st.end();
 }
 
+int fcirc_matvec_ssa(const uint64_t *a, const uint64_t *x, uint64_t *c, uint32_t K, uint32_t f_exp, uint64_t n,
+                     uint64_t batch, void *stream)
+{
+    set_error("");
+    if (!a || !x || !c) return fail(FCIRC_EINVAL, "fcirc_matvec_ssa: null pointer");
+    if (K != 64 && K != 128) return fail(FCIRC_EINVAL, "fcirc_matvec_ssa: K = %u (64 or 128)", K);
+    if (!is_pow2(n) || n < 8 || n > 512 || n > 4ull * K)
+        return fail(FCIRC_EINVAL, "fcirc_matvec_ssa: n = %llu must be a power of two in [8, min(512, 4K)]",
+                    (unsigned long long)n);
+    if (f_exp >= 2 * K) return fail(FCIRC_EINVAL, "fcirc_matvec_ssa: f = 2^%u with the exponent above 2K", f_exp);
+    if (batch == 0) return FCIRC_OK;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const int m = ilog2(n), L = m - 1;
+    SParams P{};
+    FCIRC_TRY(ssa_tables(K, f_exp, n, &P.tw, &P.itw));
+    const size_t bytes = n * batch * (K / 64 + 1) * 8;
+    Arg aa{a, bytes, true, false}, ax{x, bytes, true, false}, ac{c, bytes, false, true};
+    Staging st;
+    st.args = {&aa, &ax, &ac};
+    FCIRC_TRY(st.begin(s, 0));
+    P.a = static_cast<const uint64_t *>(aa.d);
+    P.x = static_cast<const uint64_t *>(ax.d);
+    P.c = static_cast<uint64_t *>(ac.d);
+    P.batch = batch;
+    P.scale_exp = (int)((2 * K - L) % (2 * K));
+    FCIRC_TRY(launch_sfwd(P, (int)K, m, s));
+    return st.end();
+}
+
 int fcirc_matvec_backward(const float *a, const float *x, const float *g, double f_re, double f_im,
                           float *grad_a, float *grad_x, uint64_t n, uint64_t batch, void *stream)
 {

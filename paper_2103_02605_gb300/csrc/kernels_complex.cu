@@ -31,6 +31,7 @@
 #include "kernels_complex.hpp"
 #include "prof.hpp"
 #include "gfp2.hpp"
+#include "ssa.cuh"
 #include "ring.hpp"
 
 namespace fcirc {
@@ -45,6 +46,9 @@ __device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(
 __device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
 __device__ __forceinline__ float2 cconj(float2 a) { return make_float2(a.x, -a.y); }
 __device__ __forceinline__ float2 cneg(float2 a) { return make_float2(-a.x, -a.y); }
+
+__device__ __forceinline__ float2 ld_tw(const float2 *p) { return __ldg(p); }
+__device__ __forceinline__ uint2 ld_tw(const uint2 *p) { return __ldg(p); }
 
 // The same four operations in GF(p^2) = Z/pZ[sqrt 3], p = 2^31 - 1 (the
 // paper's own field, Section 3.1), an element (x, y) = x + y sqrt 3.
@@ -69,18 +73,20 @@ struct CShape {
 };
 
 // One product's data in shared memory: row-vector side R and vector side X.
-// T: float2 (complex FP32) or uint2 (GF(p^2), gfp2.hpp); the arithmetic
-// comes from the cmul / cadd / csub / cneg overloads.
-template <class T>
+// T: the element type -- float2 (complex FP32), uint2 (GF(p^2), gfp2.hpp)
+// or SsaE<W> (Z/(2^K + 1), ssa.cuh); TW: the twiddle type (T itself, or a
+// shift amount for Z/(2^K + 1)).  The arithmetic comes from the cmul /
+// cadd / csub / cneg overloads and ld_tw.
+template <class T, class TW = T>
 struct SideT {
     T *R, *X;
-    const T *tw, *itw;   // heap-indexed twiddles and inverses, [N/2]
+    const TW *tw, *itw;   // heap-indexed twiddles and inverses, [N/2]
 };
 using Side = SideT<float2>;
 
 // forward stage S (levels d0 .. d0+nl-1) on both sides
-template <int M, int S, class T>
-__device__ __forceinline__ void cfwd_stage(SideT<T> &sd, int t)
+template <int M, int S, class T, class TW>
+__device__ __forceinline__ void cfwd_stage(SideT<T, TW> &sd, int t)
 {
     using Sh = CShape<M>;
     constexpr int NL = Sh::nl(S), D0 = Sh::d0(S), G = 8 >> NL, MM = 1 << NL;
@@ -101,7 +107,7 @@ __device__ __forceinline__ void cfwd_stage(SideT<T> &sd, int t)
             const int hh = MM >> (d + 1);
 #pragma unroll
             for (int j = 0; j < (1 << d); ++j) {
-                const T s = __ldg(&sd.tw[(1 << (D0 + d)) + (blk << d) + j]);
+                const TW s = ld_tw(&sd.tw[(1 << (D0 + d)) + (blk << d) + j]);
 #pragma unroll
                 for (int i = 0; i < hh; ++i) {
                     const int lo = (j << (NL - d)) + i, hi = lo + hh;
@@ -124,8 +130,8 @@ __device__ __forceinline__ void cfwd_stage(SideT<T> &sd, int t)
 }
 
 // recombination stage S (levels d0+nl-1 .. d0), result in R
-template <int M, int S, class T>
-__device__ __forceinline__ void crec_stage(SideT<T> &sd, int t)
+template <int M, int S, class T, class TW>
+__device__ __forceinline__ void crec_stage(SideT<T, TW> &sd, int t)
 {
     using Sh = CShape<M>;
     constexpr int NL = Sh::nl(S), D0 = Sh::d0(S), G = 8 >> NL, MM = 1 << NL;
@@ -143,7 +149,7 @@ __device__ __forceinline__ void crec_stage(SideT<T> &sd, int t)
             const int hh = MM >> (d + 1);
 #pragma unroll
             for (int j = 0; j < (1 << d); ++j) {
-                const T si = __ldg(&sd.itw[(1 << (D0 + d)) + (blk << d) + j]);
+                const TW si = ld_tw(&sd.itw[(1 << (D0 + d)) + (blk << d) + j]);
 #pragma unroll
                 for (int i = 0; i < hh; ++i) {
                     const int lo = (j << (NL - d)) + i, hi = lo + hh;
@@ -160,8 +166,8 @@ __device__ __forceinline__ void crec_stage(SideT<T> &sd, int t)
 
 // last stage: 8 contiguous numbers at 8t: levels L-2, L-1, four 2x2
 // leaves, recombination L-1, L-2; result in R
-template <int M, class T>
-__device__ __forceinline__ void cleaf_stage(SideT<T> &sd, int t)
+template <int M, class T, class TW>
+__device__ __forceinline__ void cleaf_stage(SideT<T, TW> &sd, int t)
 {
     constexpr int L = M - 1;
     T r[8], x[8];
@@ -170,8 +176,8 @@ __device__ __forceinline__ void cleaf_stage(SideT<T> &sd, int t)
         r[i] = sd.R[8 * t + i];
         x[i] = sd.X[8 * t + i];
     }
-    const T s0 = __ldg(&sd.tw[(1 << (L - 2)) + t]);
-    const T s1[2] = {__ldg(&sd.tw[(1 << (L - 1)) + 2 * t]), __ldg(&sd.tw[(1 << (L - 1)) + 2 * t + 1])};
+    const TW s0 = ld_tw(&sd.tw[(1 << (L - 2)) + t]);
+    const TW s1[2] = {ld_tw(&sd.tw[(1 << (L - 1)) + 2 * t]), ld_tw(&sd.tw[(1 << (L - 1)) + 2 * t + 1])};
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
         const T tr = cmul(s0, r[i + 4]), tx = cmul(s0, x[i]);
@@ -196,14 +202,14 @@ __device__ __forceinline__ void cleaf_stage(SideT<T> &sd, int t)
     // leaves (2q, 2q+1): the phi-circulant [[a0, a1], [phi a1, a0]], phi = +-s_{L-1}
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-        const T phi = (q & 1) ? cneg(s1[q >> 1]) : s1[q >> 1];
+        const TW phi = (q & 1) ? cneg(s1[q >> 1]) : s1[q >> 1];
         const T a0 = r[2 * q], a1 = r[2 * q + 1], y0 = x[2 * q], y1 = x[2 * q + 1];
         const T a1f = cmul(phi, a1);
         r[2 * q] = cadd(cmul(a0, y0), cmul(a1, y1));
         r[2 * q + 1] = cadd(cmul(a1f, y0), cmul(a0, y1));
     }
-    const T i1[2] = {__ldg(&sd.itw[(1 << (L - 1)) + 2 * t]), __ldg(&sd.itw[(1 << (L - 1)) + 2 * t + 1])};
-    const T i0 = __ldg(&sd.itw[(1 << (L - 2)) + t]);
+    const TW i1[2] = {ld_tw(&sd.itw[(1 << (L - 1)) + 2 * t]), ld_tw(&sd.itw[(1 << (L - 1)) + 2 * t + 1])};
+    const TW i0 = ld_tw(&sd.itw[(1 << (L - 2)) + t]);
 #pragma unroll
     for (int hb = 0; hb < 2; ++hb)
 #pragma unroll
@@ -224,33 +230,33 @@ __device__ __forceinline__ void cleaf_stage(SideT<T> &sd, int t)
 }
 
 // whole product for one instance: forward stages, last stage, recombination
-template <int M, int S, class T>
-__device__ __forceinline__ void cfwd_all(SideT<T> &sd, int t)
+template <int M, int S, class T, class TW>
+__device__ __forceinline__ void cfwd_all(SideT<T, TW> &sd, int t)
 {
     if constexpr (S < CShape<M>::NST) {
-        cfwd_stage<M, S, T>(sd, t);
+        cfwd_stage<M, S, T, TW>(sd, t);
         __syncthreads();
-        cfwd_all<M, S + 1, T>(sd, t);
+        cfwd_all<M, S + 1, T, TW>(sd, t);
     }
 }
 
-template <int M, int S, class T>
-__device__ __forceinline__ void crec_all(SideT<T> &sd, int t)
+template <int M, int S, class T, class TW>
+__device__ __forceinline__ void crec_all(SideT<T, TW> &sd, int t)
 {
     if constexpr (S >= 0) {
-        crec_stage<M, S, T>(sd, t);
+        crec_stage<M, S, T, TW>(sd, t);
         __syncthreads();
-        crec_all<M, S - 1, T>(sd, t);
+        crec_all<M, S - 1, T, TW>(sd, t);
     }
 }
 
-template <int M, class T>
-__device__ __forceinline__ void cproduct(SideT<T> &sd, int t)
+template <int M, class T, class TW>
+__device__ __forceinline__ void cproduct(SideT<T, TW> &sd, int t)
 {
-    cfwd_all<M, 0, T>(sd, t);
-    cleaf_stage<M, T>(sd, t);
+    cfwd_all<M, 0, T, TW>(sd, t);
+    cleaf_stage<M, T, TW>(sd, t);
     __syncthreads();
-    crec_all<M, CShape<M>::NST - 1, T>(sd, t);
+    crec_all<M, CShape<M>::NST - 1, T, TW>(sd, t);
 }
 
 template <int M>
@@ -271,7 +277,7 @@ __global__ void __launch_bounds__(CShape<M>::CT) k_cfwd(const __grid_constant__ 
         sd.X[e] = live ? x[e] : make_float2(0.f, 0.f);
     }
     __syncthreads();
-    cproduct<M, float2>(sd, t);
+    cproduct<M, float2, float2>(sd, t);
     if (live) {
         float2 *c = reinterpret_cast<float2 *>(P.c) + inst * Sh::N;
 #pragma unroll
@@ -303,7 +309,7 @@ __global__ void __launch_bounds__(CShape<M>::CT) k_gfwd(const __grid_constant__ 
         sd.X[e] = live ? x[e] : make_uint2(0u, 0u);
     }
     __syncthreads();
-    cproduct<M, uint2>(sd, t);
+    cproduct<M, uint2, uint2>(sd, t);
     if (live) {
         uint2 *c = reinterpret_cast<uint2 *>(P.c) + inst * Sh::N;
         const uint2 sc = make_uint2(P.scale, 0u);
@@ -311,6 +317,41 @@ __global__ void __launch_bounds__(CShape<M>::CT) k_gfwd(const __grid_constant__ 
         for (int k = 0; k < 8; ++k) {
             const int e = t + Sh::NTI * k;
             c[e] = cmul(sd.R[e], sc);
+        }
+    }
+}
+
+// Products over Z/(2^K + 1), K = 64 W (ssa.cuh): twiddles are shifts; the
+// deferred halvings are one shift by 2K - L at the end.
+template <int M, int W>
+__global__ void __launch_bounds__(CShape<M>::CT) k_sfwd(const __grid_constant__ SParams P)
+{
+    using Sh = CShape<M>;
+    using E = SsaE<W>;
+    extern __shared__ __align__(16) unsigned char ssm[];
+    E *sbase = reinterpret_cast<E *>(ssm);
+    const int li = threadIdx.x / Sh::NTI, t = threadIdx.x % Sh::NTI;
+    const uint64_t inst = (uint64_t)blockIdx.x * Sh::IPC + li;
+    const bool live = inst < P.batch;
+    SideT<E, SsaTw<W>> sd{sbase + (size_t)li * 2 * Sh::N, sbase + (size_t)li * 2 * Sh::N + Sh::N,
+                          reinterpret_cast<const SsaTw<W> *>(P.tw), reinterpret_cast<const SsaTw<W> *>(P.itw)};
+    const E *a = reinterpret_cast<const E *>(P.a) + inst * Sh::N;
+    const E *x = reinterpret_cast<const E *>(P.x) + inst * Sh::N;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        const int e = t + Sh::NTI * k;
+        sd.R[e] = live ? a[e] : ssa_zero<W>();
+        sd.X[e] = live ? x[e] : ssa_zero<W>();
+    }
+    __syncthreads();
+    cproduct<M, E, SsaTw<W>>(sd, t);
+    if (live) {
+        E *c = reinterpret_cast<E *>(P.c) + inst * Sh::N;
+        const SsaTw<W> sc{P.scale_exp};
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            const int e = t + Sh::NTI * k;
+            c[e] = cmul(sc, sd.R[e]);
         }
     }
 }
@@ -344,8 +385,8 @@ __global__ void __launch_bounds__(CShape<M>::CT) k_cbwd(const __grid_constant__ 
         sa.X[e] = live ? cconj(x[e]) : z;
     }
     __syncthreads();
-    cproduct<M, float2>(sx, t);
-    cproduct<M, float2>(sa, t);
+    cproduct<M, float2, float2>(sx, t);
+    cproduct<M, float2, float2>(sa, t);
     if (live) {
         float2 *gx = reinterpret_cast<float2 *>(P.grad_x) + inst * Sh::N;
         float2 *ga = reinterpret_cast<float2 *>(P.grad_a) + inst * Sh::N;
@@ -458,6 +499,54 @@ int get_gtables(uint32_t fre, uint32_t fim, uint64_t n, const uint2 **tw, const 
     return FCIRC_OK;
 }
 
+// Z/(2^K + 1) twiddles per (K, f = 2^fe, n): exponents mod 2K of
+// s_{l,j} = rho^(2^(L-l-1)) psi_{2^(l+1)}^brv(j), rho = 2^(fe / 2^L),
+// psi_m = 2^(2K/m); inverses 2^(2K - e).
+struct SPlanKey {
+    int dev;
+    uint32_t K, fe;
+    uint64_t n;
+    bool operator<(const SPlanKey &o) const { return std::tie(dev, K, fe, n) < std::tie(o.dev, o.K, o.fe, o.n); }
+};
+std::map<SPlanKey, std::pair<int *, int *>> g_splans;
+
+int get_stables(uint32_t K, uint32_t fe, uint64_t n, const int **tw, const int **itw)
+{
+    int dev = 0;
+    FCIRC_CUDA_TRY(cudaGetDevice(&dev));
+    const SPlanKey key{dev, K, fe, n};
+    std::lock_guard<std::mutex> lk(g_cmu);
+    auto it = g_splans.find(key);
+    if (it == g_splans.end()) {
+        const int m = ilog2(n), L = m - 1;
+        const uint64_t twoK = 2ull * K;
+        if ((((uint64_t)1 << L) > twoK) || (fe % ((uint64_t)1 << L)) != 0)
+            return fail(FCIRC_ENOROOT, "Z/(2^%u + 1): f = 2^%u has no 2^%d-th root that is a power of 2", K, fe, L);
+        const uint64_t er = fe >> L;
+        std::vector<int> h(n / 2), hi(n / 2);
+        h[0] = hi[0] = 0;
+        for (int l = 0; l < L; ++l)
+            for (uint64_t j = 0; j < ((uint64_t)1 << l); ++j) {
+                const uint64_t e = (er * ((uint64_t)1 << (L - l - 1)) + (twoK >> (l + 1)) * host::bitrev(j, l)) % twoK;
+                h[((size_t)1 << l) + j] = (int)e;
+                hi[((size_t)1 << l) + j] = (int)((twoK - e) % twoK);
+            }
+        int *d = nullptr, *di = nullptr;
+        if (dev_alloc((void **)&d, n / 2 * sizeof(int)) != cudaSuccess ||
+            dev_alloc((void **)&di, n / 2 * sizeof(int)) != cudaSuccess) {
+            (void)cudaGetLastError();
+            cudaFree(d);
+            return fail(FCIRC_ENOMEM, "Z/(2^K+1) plan: cudaMalloc failed");
+        }
+        FCIRC_CUDA_TRY(cudaMemcpy(d, h.data(), n / 2 * sizeof(int), cudaMemcpyHostToDevice));
+        FCIRC_CUDA_TRY(cudaMemcpy(di, hi.data(), n / 2 * sizeof(int), cudaMemcpyHostToDevice));
+        it = g_splans.emplace(key, std::make_pair(d, di)).first;
+    }
+    *tw = it->second.first;
+    *itw = it->second.second;
+    return FCIRC_OK;
+}
+
 template <class K>
 int set_smem(K kernel, int bytes)
 {
@@ -489,6 +578,35 @@ int launch_gfwd_m(const GParams &P, cudaStream_t s)
     k_gfwd<M><<<(unsigned)grid, Sh::CT, smem, s>>>(P);
     FCIRC_CUDA_TRY(cudaGetLastError());
     return FCIRC_OK;
+}
+
+template <int M, int W>
+int launch_sfwd_mw(const SParams &P, cudaStream_t s)
+{
+    using Sh = CShape<M>;
+    const int smem = Sh::IPC * 2 * Sh::N * (int)sizeof(SsaE<W>);
+    if (smem > 227 * 1024) return fail(FCIRC_EINVAL, "Z/(2^K+1) product: n = %d too large for K = %d", Sh::N, 64 * W);
+    FCIRC_TRY(set_smem(k_sfwd<M, W>, smem));
+    const uint64_t grid = (P.batch + Sh::IPC - 1) / Sh::IPC;
+    ProfScope ps("k_sfwd", s);
+    k_sfwd<M, W><<<(unsigned)grid, Sh::CT, smem, s>>>(P);
+    FCIRC_CUDA_TRY(cudaGetLastError());
+    return FCIRC_OK;
+}
+
+template <int W>
+int launch_sfwd_w(const SParams &P, int m, cudaStream_t s)
+{
+    switch (m) {
+    case 3: return launch_sfwd_mw<3, W>(P, s);
+    case 4: return launch_sfwd_mw<4, W>(P, s);
+    case 5: return launch_sfwd_mw<5, W>(P, s);
+    case 6: return launch_sfwd_mw<6, W>(P, s);
+    case 7: return launch_sfwd_mw<7, W>(P, s);
+    case 8: return launch_sfwd_mw<8, W>(P, s);
+    case 9: return launch_sfwd_mw<9, W>(P, s);
+    default: return fail(FCIRC_EINVAL, "Z/(2^K+1) product: n = 2^%d not supported", m);
+    }
 }
 
 template <int M>
@@ -523,6 +641,25 @@ void release_cplans()
         cudaFree(kv.second.second);
     }
     g_gplans.clear();
+    for (auto &kv : g_splans) {
+        cudaSetDevice(kv.first.dev);
+        cudaDeviceSynchronize();
+        cudaFree(kv.second.first);
+        cudaFree(kv.second.second);
+    }
+    g_splans.clear();
+}
+
+int ssa_tables(uint32_t K, uint32_t fe, uint64_t n, const int **tw, const int **itw)
+{
+    return get_stables(K, fe, n, tw, itw);
+}
+
+int launch_sfwd(const SParams &P, int K, int m, cudaStream_t s)
+{
+    if (K == 64) return launch_sfwd_w<1>(P, m, s);
+    if (K == 128) return launch_sfwd_w<2>(P, m, s);
+    return fail(FCIRC_EINVAL, "Z/(2^K+1) product: K = %d not supported (64 or 128)", K);
 }
 
 int gf_tables(uint32_t fre, uint32_t fim, uint64_t n, const uint2 **tw, const uint2 **itw)

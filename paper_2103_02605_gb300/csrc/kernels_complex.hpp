@@ -33,6 +33,18 @@ struct GParams {
 };
 
 int gf_tables(uint32_t fre, uint32_t fim, uint64_t n, const uint2 **tw, const uint2 **itw);
+
+// Z/(2^K + 1), K = 64 W (ssa.cuh): elements of W + 1 uint64 words.
+struct SParams {
+    const uint64_t *a, *x;
+    uint64_t *c;
+    const int *tw, *itw;   // twiddle exponents mod 2K
+    uint64_t batch;
+    int scale_exp;         // 2^-L = 2^(2K - L)
+};
+
+int ssa_tables(uint32_t K, uint32_t fe, uint64_t n, const int **tw, const int **itw);
+int launch_sfwd(const SParams &P, int K, int m, cudaStream_t s);
 int launch_gfwd(const GParams &P, int m, cudaStream_t s);
 
 // Twiddles s_{l,j} of the product with parameter f and size n (FP64

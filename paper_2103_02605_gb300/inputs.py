@@ -142,6 +142,40 @@ def bigint_pair(bits: int = 1 << 26, seed: int = SEED_BASE + 4):
     return g.uniform_u16(bits // 16), g.uniform_u16(bits // 16)
 
 
+def ssa_to_words(values, K: int) -> np.ndarray:
+    """Elements of Z/(2^K + 1) (Python ints in [0, 2^K]) in the library's
+    layout: K/64 little-endian uint64 words and a top word per element."""
+    W = K // 64
+    out = np.zeros((len(values), W + 1), np.uint64)
+    for i, v in enumerate(values):
+        assert 0 <= v <= (1 << K)
+        if v == 1 << K:
+            out[i, W] = 1
+        else:
+            for j in range(W):
+                out[i, j] = (v >> (64 * j)) & 0xFFFFFFFFFFFFFFFF
+    return out
+
+
+def ssa_from_words(words) -> list:
+    w = np.asarray(words, np.uint64)
+    W = w.shape[-1] - 1
+    return [sum(int(row[j]) << (64 * j) for j in range(W)) + (int(row[W]) << (64 * W)) for row in w.reshape(-1, W + 1)]
+
+
+def ssa_elements(n: int, K: int, seed: int) -> list:
+    """Elements of Z/(2^K + 1) of K random bits each from the seeded
+    generator, with the edge values 0, 1, 2^K - 1 and 2^K planted at the
+    first positions."""
+    W = K // 64
+    words = SplitMix64(seed).next_u64(n * W).reshape(n, W)
+    vals = [sum(int(words[i, j]) << (64 * j) for j in range(W)) for i in range(n)]
+    for i, e in enumerate((0, 1, (1 << K) - 1, 1 << K)):
+        if i < n:
+            vals[i] = e
+    return vals
+
+
 def limbs_to_int(limbs) -> int:
     """Python int from little-endian 16-bit limbs (exact)."""
     b = np.ascontiguousarray(limbs, dtype="<u2").tobytes()

@@ -122,3 +122,32 @@ def test_unmutated_oracle_passes_every_pin_call():
     failure under a mutant is caused by the planted mistake."""
     for call in PIN_CALLS:
         call(O)
+
+
+def _ssa_mutant_drop_f(K, f_exp, a, x):
+    """The Z/(2^K + 1) oracle with the wrap factor f dropped."""
+    M = (1 << K) + 1
+    n = len(a)
+    return [sum(a[k] * x[(i + k) % n] for k in range(n)) % M for i in range(n)]
+
+
+def _ssa_mutant_wrong_index(K, f_exp, a, x):
+    """The Z/(2^K + 1) oracle with the vector index mirrored."""
+    M = (1 << K) + 1
+    f = pow(2, f_exp, M)
+    n = len(a)
+    return [sum(a[k] * x[(i - k) % n] * (f if i + k >= n else 1) for k in range(n)) % M for i in range(n)]
+
+
+@pytest.mark.parametrize("mutant", [_ssa_mutant_drop_f, _ssa_mutant_wrong_index])
+def test_pins_catch_ssa_oracle_mutants(mutant):
+    class Shim:
+        fcirc_matvec_ssa = staticmethod(mutant)
+    caught = False
+    for call in (lambda o: pins.test_ssa_oracle_small_values_are_the_integer_product(o, 8),
+                 lambda o: pins.test_ssa_oracle_identity_and_shift_rows(o, 64)):
+        try:
+            call(Shim)
+        except AssertionError:
+            caught = True
+    assert caught

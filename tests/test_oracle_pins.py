@@ -279,6 +279,35 @@ def test_gf_oracle_shift_and_identity_rows(orc, n):
     assert (int(got[-1, 0]), int(got[-1, 1])) == ((fr * xr + 3 * fi * xi) % GFP, (fr * xi + fi * xr) % GFP)
 
 
+# -- the ring Z/(2^K + 1) of Schoenhage-Strassen multiplication -------------------
+
+@pytest.mark.parametrize("n", [1, 2, 8, 32])
+def test_ssa_oracle_small_values_are_the_integer_product(orc, n):
+    """Entries below 2^8 keep every sum far below 2^64: the ring product with
+    f = 1 is the integer cyclic correlation (numpy), and with f = -1 (2^K) the
+    wrapped terms change sign (Definition 2)."""
+    rng = np.random.default_rng(800 + n)
+    a = rng.integers(0, 256, n)
+    x = rng.integers(0, 256, n)
+    corr = [int(sum(a[k] * x[(i + k) % n] for k in range(n))) for i in range(n)]
+    assert orc.fcirc_matvec_ssa(64, 0, [int(v) for v in a], [int(v) for v in x]) == corr
+    M = (1 << 64) + 1
+    neg = [int(sum((1 if i + k < n else -1) * a[k] * x[(i + k) % n] for k in range(n))) % M for i in range(n)]
+    assert orc.fcirc_matvec_ssa(64, 64, [int(v) for v in a], [int(v) for v in x]) == neg
+
+
+@pytest.mark.parametrize("K", [64, 128])
+def test_ssa_oracle_identity_and_shift_rows(orc, K):
+    n = 8
+    M = (1 << K) + 1
+    x = I.ssa_elements(n, K, seed=K)
+    e0 = [1] + [0] * (n - 1)
+    assert orc.fcirc_matvec_ssa(K, 5, e0, x) == x
+    e1 = [0, 1] + [0] * (n - 2)
+    got = orc.fcirc_matvec_ssa(K, 5, e1, x)
+    assert got[:-1] == x[1:] and got[-1] == (x[0] << 5) % M
+
+
 # -- the paper's Algorithm 1 (brute force) agrees with the dense oracle ----------
 
 @pytest.mark.parametrize("n", [1, 2, 4, 8, 16, 32])
