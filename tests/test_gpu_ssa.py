@@ -25,7 +25,7 @@ def dev(words):
     return torch.from_numpy(np.ascontiguousarray(words, np.uint64).view(np.int64)).cuda()
 
 
-@pytest.mark.parametrize("K,n", [(64, 8), (64, 16), (64, 64), (64, 256), (128, 8), (128, 32), (128, 512)])
+@pytest.mark.parametrize("K,n", [(64, 8), (64, 16), (64, 64), (64, 256), (128, 8), (128, 32), (128, 256), (128, 512)])
 def test_ssa_products_vs_oracle(F, orc, K, n):
     import torch
     batch = 2
@@ -51,5 +51,8 @@ def test_ssa_errors(F):
     assert L.fcirc_matvec_ssa(z.data_ptr(), z.data_ptr(), z.data_ptr(), 64, 0, 512, 1, None) == 1
     assert L.fcirc_matvec_ssa(z.data_ptr(), z.data_ptr(), z.data_ptr(), 64, 128, 8, 1, None) == 1
     assert L.fcirc_matvec_ssa(z.data_ptr(), z.data_ptr(), z.data_ptr(), 64, 1, 8, 1, None) == 2   # 4 does not divide 1
+    zz = torch.zeros(3 * 512, dtype=torch.int64, device="cuda")
+    # -1 = 2^128 has no 2^8-th root among the powers of 2 in Z/(2^128 + 1)
+    assert L.fcirc_matvec_ssa(zz.data_ptr(), zz.data_ptr(), zz.data_ptr(), 128, 128, 512, 1, None) == 2
     assert L.fcirc_matvec_ssa(None, z.data_ptr(), z.data_ptr(), 64, 0, 8, 1, None) == 1
     assert L.fcirc_matvec_ssa(z.data_ptr(), z.data_ptr(), z.data_ptr(), 64, 0, 8, 0, None) == 0
