@@ -367,18 +367,25 @@ static int poly_core(const uint16_t *P, uint64_t np, const uint16_t *Q, uint64_t
         }
         FCIRC_TRY(run_fwd_pass(i, jd, 6, 3, s));
     }
+    // The reversed-row embedding moves the product up by one entry
+    // (coefficient k is circulant entry k + 1).  The 4096-residue tile kernel
+    // undoes that in its leaves (TILE_SHIFT: the row vector shifted by one
+    // place, an identity at f = 1), so the CRT writes whole aligned sectors;
+    // the other tile kernels leave it to the CRT (EPI_CRT_ROT).
+    const bool shift = fast_tile_ok(p0.logT);
     {
         TileParams tp;
         for (int q = 0; q < 3; ++q) tp.job[q] = tile_job(pl[q], src_u32(A[q], N), src_u32(X[q], N), A[q], 1);
         tp.N = N;
         tp.logT = p0.logT;
         tp.D = p0.D;
+        tp.var = shift ? TILE_SHIFT : TILE_FULL;
         FCIRC_TRY(run_tile(tp, (uint64_t)1 << p0.k, 3, s));
     }
     for (int i = p0.npass - 1; i >= 0; --i) {
         InvDesc jd[3];
         for (int q = 0; q < 3; ++q) jd[q] = InvDesc{A[q], A[q], pl[q]};
-        FCIRC_TRY(run_inv_pass(i, jd, 3, i == 0 ? EPI_CRT_ROT : EPI_LAZY, out, nout, &crt, s));
+        FCIRC_TRY(run_inv_pass(i, jd, 3, i == 0 ? (shift ? EPI_CRT : EPI_CRT_ROT) : EPI_LAZY, out, nout, &crt, s));
     }
     return FCIRC_OK;
 }

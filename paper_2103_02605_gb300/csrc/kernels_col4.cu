@@ -543,17 +543,44 @@ __device__ __forceinline__ void c4inv_stage(const ColInvParams &P, uint32_t *sm,
     for (int q = 0; q < NP; ++q) c4inv_job<LF, S>(P, P.job[q], sm + q * C4<LF>::WORDS, base, pb, logS, tid);
 }
 
+// The CRT of one quad (circulant entries idx .. idx+3, the three primes'
+// canonical residues in r1, r2, r3) into the int64 coefficients.  EPI_CRT:
+// entry k is coefficient k, and an in-range quad leaves as one 32-byte store
+// (a whole DRAM sector) when the output is 32-byte aligned.  EPI_CRT_ROT:
+// coefficient k is circulant entry k + 1, four 8-byte stores.
+__device__ __forceinline__ void crt_store4(const ColInvParams &P, uint32_t idx, uint4 r1, uint4 r2, uint4 r3)
+{
+    const uint64_t e0 = crt3(r1.x, r2.x, r3.x, P.crt), e1 = crt3(r1.y, r2.y, r3.y, P.crt);
+    const uint64_t e2 = crt3(r1.z, r2.z, r3.z, P.crt), e3 = crt3(r1.w, r2.w, r3.w, P.crt);
+    if (P.epi == EPI_CRT) {
+        if ((reinterpret_cast<uintptr_t>(P.dst64) & 31) == 0 && (uint64_t)idx + 3 < P.nout) {
+            asm volatile("st.global.v4.u64 [%0], {%1, %2, %3, %4};\n" ::"l"(P.dst64 + idx), "l"(e0), "l"(e1),
+                         "l"(e2), "l"(e3)
+                         : "memory");
+        } else {
+            if (idx < P.nout) P.dst64[idx] = e0;
+            if (idx + 1 < P.nout) P.dst64[idx + 1] = e1;
+            if (idx + 2 < P.nout) P.dst64[idx + 2] = e2;
+            if (idx + 3 < P.nout) P.dst64[idx + 3] = e3;
+        }
+    } else {
+        const uint32_t d0 = (idx + P.N - 1) & (P.N - 1);   // coefficient k is circulant entry k + 1
+        if (d0 < P.nout) P.dst64[d0] = e0;
+        if (idx < P.nout) P.dst64[idx] = e1;
+        if (idx + 1 < P.nout) P.dst64[idx + 1] = e2;
+        if (idx + 2 < P.nout) P.dst64[idx + 2] = e3;
+    }
+}
+
 // CRT phase of the polynomial product: the rows of the store phase, the three
 // primes' canonical residues from the CTA that computed them, Garner's CRT,
-// and the int64 coefficient stored rotated by one (coefficient k is circulant
-// entry k + 1).
+// and the int64 coefficients (crt_store4).
 template <int LF>
 __device__ __forceinline__ void c4_crt_phase(const ColInvParams &P, const uint32_t *sm, uint32_t base0, int logS,
                                              int rank, int tid)
 {
     using Sh = C4<LF>;
     constexpr int RSTEP = kC4Threads >> Sh::LCQ;
-    const uint32_t mask = P.N - 1;
     const int cq = tid & ((1 << Sh::LCQ) - 1);
     const int row_t = (rank << Sh::LRW) + (tid >> Sh::LCQ);
     const uint32_t sb = c4_seg_base<LF>(sm, cq);
@@ -564,12 +591,7 @@ __device__ __forceinline__ void c4_crt_phase(const ColInvParams &P, const uint32
         const uint4 r1 = c4_seg_ld<LF>(sb, cq, row);
         const uint4 r2 = c4_seg_ld<LF>(sb + PB, cq, row);
         const uint4 r3 = c4_seg_ld<LF>(sb + 2 * PB, cq, row);
-        const uint32_t idx = base0 + ((uint32_t)cq << 2) + ((uint32_t)row << logS);
-        const uint32_t d0 = (idx + mask) & mask;   // coefficient k is circulant entry k + 1
-        if (d0 < P.nout) P.dst64[d0] = crt3(r1.x, r2.x, r3.x, P.crt);
-        if (idx < P.nout) P.dst64[idx] = crt3(r1.y, r2.y, r3.y, P.crt);
-        if (idx + 1 < P.nout) P.dst64[idx + 1] = crt3(r1.z, r2.z, r3.z, P.crt);
-        if (idx + 2 < P.nout) P.dst64[idx + 2] = crt3(r1.w, r2.w, r3.w, P.crt);
+        crt_store4(P, base0 + ((uint32_t)cq << 2) + ((uint32_t)row << logS), r1, r2, r3);
     }
 }
 
@@ -600,7 +622,7 @@ __global__ void __cluster_dims__(C4<LF>::CL, 1, 1) __launch_bounds__(kC4Threads,
     c4inv_stage<LF, NP, 0>(P, sm, base, pb, logS, tid);
     grp_arrive<Sh::CL>();
     grp_wait<Sh::CL>();
-    if (NP == 3 && P.epi == EPI_CRT_ROT) {
+    if (NP == 3 && epi_crt(P.epi)) {
         c4_crt_phase<LF>(P, sm, base0, logS, rank, tid);
     } else {
 #pragma unroll 1
@@ -616,8 +638,7 @@ __global__ void __cluster_dims__(C4<LF>::CL, 1, 1) __launch_bounds__(kC4Threads,
 // shared memory (so two clusters' CTAs share an SM and overlap their memory
 // and arithmetic phases); then each CTA takes a third of the group's rows,
 // gathers the three canonical residues through distributed shared memory,
-// and writes the CRT result rotated by one (coefficient k is circulant entry
-// k + 1).
+// and writes the CRT results (crt_store4).
 template <int LF>
 __global__ void __cluster_dims__(3, 1, 1) __launch_bounds__(kC4Threads, 2)
     k_colinv4x3(const __grid_constant__ ColInvParams P)
@@ -650,18 +671,12 @@ __global__ void __cluster_dims__(3, 1, 1) __launch_bounds__(kC4Threads, 2)
     const int w0 = q * W3, w1 = (q + 1) * W3 < W ? (q + 1) * W3 : W;
     const uint32_t own = smem_addr(sm);
     const uint32_t s1 = cl_map(own, 0), s2 = cl_map(own, 1), s3 = cl_map(own, 2);
-    const uint32_t mask = P.N - 1;
 #pragma unroll 2
     for (int w = w0 + tid; w < w1; w += kC4Threads) {
         const int quad = w & ((1 << Sh::LNQ) - 1), row = w >> Sh::LNQ;
         const uint32_t off = 4u * (uint32_t)c4_off<LF>(quad, row);
         const uint4 r1 = cl_ld4(s1 + off), r2 = cl_ld4(s2 + off), r3 = cl_ld4(s3 + off);
-        const uint32_t idx = base + ((uint32_t)quad << 2) + ((uint32_t)row << logS);
-        const uint32_t d0 = (idx + mask) & mask;
-        if (d0 < P.nout) P.dst64[d0] = crt3(r1.x, r2.x, r3.x, P.crt);
-        if (idx < P.nout) P.dst64[idx] = crt3(r1.y, r2.y, r3.y, P.crt);
-        if (idx + 1 < P.nout) P.dst64[idx + 1] = crt3(r1.z, r2.z, r3.z, P.crt);
-        if (idx + 2 < P.nout) P.dst64[idx + 2] = crt3(r1.w, r2.w, r3.w, P.crt);
+        crt_store4(P, base + ((uint32_t)quad << 2) + ((uint32_t)row << logS), r1, r2, r3);
     }
     cl_arrive();
     cl_wait();   // no CTA leaves while a peer still reads its shared memory
@@ -773,9 +788,9 @@ bool col4_inv_ok(const ColInvParams &P)
     // every cluster's column groups lie in one level-l0 block
     if (lf < 8 || lf > 12 || logS < 2 + ((12 - lf) > 3 ? 12 - lf : 3)) return false;
     // three primes only with the CRT epilogue (the three-CTA cluster kernel)
-    if (P.nprime != 1 && !(P.nprime == 3 && P.epi == EPI_CRT_ROT && FCIRC_C4_X3)) return false;
+    if (P.nprime != 1 && !(P.nprime == 3 && epi_crt(P.epi) && FCIRC_C4_X3)) return false;
     for (int q = 0; q < P.nprime; ++q)
-        if (!aligned(P.job[q].src, 16) || (P.epi != EPI_CRT_ROT && !aligned(P.job[q].dst, 16))) return false;
+        if (!aligned(P.job[q].src, 16) || (!epi_crt(P.epi) && !aligned(P.job[q].dst, 16))) return false;
     return true;
 }
 
@@ -816,7 +831,7 @@ int launch_colinv4(const ColInvParams &P, cudaStream_t s)
         case 11: return launch_c4inv_lf<11, 1>(P, s);
         case 12: return launch_c4inv_lf<12, 1>(P, s);
         }
-    } else if (P.nprime == 3 && P.epi == EPI_CRT_ROT) {
+    } else if (P.nprime == 3 && epi_crt(P.epi)) {
         switch (lf) {
         case 8: return launch_c4inv_x3<8>(P, s);
         case 9: return launch_c4inv_x3<9>(P, s);

@@ -297,7 +297,7 @@ __device__ __forceinline__ void colinv_stage(const ColInvParams &P, uint32_t *sm
                     const uint32_t val = v[hb * M + i];
                     if (!LAST)
                         smq[cphi(row, col)] = val;
-                    else if (P.epi == EPI_CRT_ROT)
+                    else if (epi_crt(P.epi))
                         smq[cphi(row, col)] = reduce_once(val, p);   // canonical, for the CRT below
                     else
                         J.dst[base + (row << logS) + col] = P.epi == EPI_CANON ? reduce_once(val, p) : val;
@@ -305,9 +305,9 @@ __device__ __forceinline__ void colinv_stage(const ColInvParams &P, uint32_t *sm
             }
         }
     }
-    if (LAST && NP == 3 && P.epi == EPI_CRT_ROT) {
+    if (LAST && NP == 3 && epi_crt(P.epi)) {
         // every residue of this thread's groups was written by this thread
-        const uint32_t mask = P.N - 1;
+        const uint32_t mask = P.N - 1, rot = P.epi == EPI_CRT_ROT ? mask : 0u;
 #pragma unroll 1
         for (int h = 0; h < 2 * B; ++h) {
             int col, row0, blk;
@@ -317,7 +317,8 @@ __device__ __forceinline__ void colinv_stage(const ColInvParams &P, uint32_t *sm
                 const uint32_t row = row0 + (i << LST);
                 const int w = cphi(row, col);
                 const uint32_t idx = base + (row << logS) + col;
-                const uint32_t dst = (idx + mask) & mask;   // coefficient k is circulant entry k + 1
+                // EPI_CRT_ROT: coefficient k is circulant entry k + 1
+                const uint32_t dst = (idx + rot) & mask;
                 if (dst < P.nout) P.dst64[dst] = crt3(sm[w], sm[R * 4 + w], sm[2 * R * 4 + w], P.crt);
             }
         }

@@ -129,12 +129,12 @@ k_strided_inv(const __grid_constant__ StrInvParams P)
         }
         __syncthreads();
     }
-    if (P.epi == EPI_CRT_ROT) {
-        const uint64_t mask = P.N - 1;
+    if (epi_crt(P.epi)) {
+        const uint64_t mask = P.N - 1, rot = P.epi == EPI_CRT_ROT ? mask : 0u;
         for (int e = threadIdx.x; e < RW; e += blockDim.x) {
             const int r = e >> logW, w = e & (W - 1);
             const uint64_t idx = base + ((uint64_t)r << logS) + w;
-            const uint64_t dst = (idx + mask) & mask;   // coefficient k is circulant entry k + 1
+            const uint64_t dst = (idx + rot) & mask;   // EPI_CRT_ROT: coefficient k is circulant entry k + 1
             if (dst < P.nout) {
                 const uint32_t r1 = reduce_once(tile[e], P.job[0].p);
                 const uint32_t r2 = reduce_once(tile[RW + e], P.job[1].p);

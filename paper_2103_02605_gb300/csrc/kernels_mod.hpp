@@ -40,14 +40,17 @@ struct TileJob {
 // transformed row vector (the leaf operands of Algorithm 1's row side, lazy
 // in [0, 4p)) for reuse with many vectors.  TILE_PLANNED: J.a is such a
 // transformed row vector (read as it is); the vector tree, the leaves and
-// the recombination.
-enum : int { TILE_FULL = 0, TILE_ROW = 1, TILE_PLANNED = 2 };
+// the recombination.  TILE_SHIFT: TILE_FULL with the row vector shifted by
+// one place in the leaves (leaf2_shift), which moves the product up by one
+// entry when f = 1: the polynomial product's reversed-row embedding then
+// needs no rotation of its output.
+enum : int { TILE_FULL = 0, TILE_ROW = 1, TILE_PLANNED = 2, TILE_SHIFT = 3 };
 
 struct TileParams {
     TileJob job[3];
     uint64_t N;
     int logT, D;
-    int var = 0;           // TILE_FULL / TILE_ROW / TILE_PLANNED (tile_dev.cuh); logT = 12 only
+    int var = 0;           // TILE_FULL / ROW / PLANNED / SHIFT (tile_dev.cuh); logT = 12 only
 };
 
 struct StrFwdJob {
@@ -71,7 +74,12 @@ struct StrInvJob {
     uint32_t p;
 };
 
-enum Epilogue { EPI_CANON = 0, EPI_LAZY = 1, EPI_CRT_ROT = 2 };
+// EPI_CRT_ROT: CRT of three primes, coefficient k taken from circulant entry
+// k + 1 (the reversed-row embedding); EPI_CRT: CRT with entry k to
+// coefficient k (the leaves already shifted the product, TILE_SHIFT).
+enum Epilogue { EPI_CANON = 0, EPI_LAZY = 1, EPI_CRT_ROT = 2, EPI_CRT = 3 };
+
+__host__ __device__ inline bool epi_crt(int e) { return e == EPI_CRT_ROT || e == EPI_CRT; }
 
 // Garner constants for (p1, p2, p3).
 struct CrtConsts {

@@ -67,7 +67,11 @@ int launch_tile_fast(const TileParams &P, uint64_t ntiles, int njobs, cudaStream
         return FCIRC_OK;
     }
     ProfScope ps("k_tile4096", s);
-    if (ma == MODE_U32 && mx == MODE_U32)
+    if (P.var == TILE_SHIFT) {
+        if (ma != MODE_U32 || mx != MODE_U32)
+            return fail(FCIRC_EINVAL, "tile kernel: shifted leaves need plain sources (%d/%d)", ma, mx);
+        k_tile4096<MODE_U32, MODE_U32, TILE_SHIFT><<<grid, 256, 0, s>>>(P);
+    } else if (ma == MODE_U32 && mx == MODE_U32)
         k_tile4096<MODE_U32, MODE_U32><<<grid, 256, 0, s>>>(P);
     else if (ma == MODE_U32_S && mx == MODE_U32)
         k_tile4096<MODE_U32_S, MODE_U32><<<grid, 256, 0, s>>>(P);

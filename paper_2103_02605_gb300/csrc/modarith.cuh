@@ -180,4 +180,23 @@ FCIRC_HD void leaf2(uint32_t &a0, uint32_t &a1, uint32_t y0, uint32_t y1, Tw phi
     a1 = redc(t1, p, pinv);
 }
 
+// The same leaf for the row vector shifted by one place (a'_k = a_(k-1),
+// indices mod n; the product's entries move up by one, c'_i = c_(i+1), when
+// the root parameter is 1).  The shift is z a(z), so the leaf's row
+// (x0, x1) = a mod (z^2 - phi) becomes (phi x1, x0):
+//   c'_0 = phi x1 y0 + x0 y1,   c'_1 = phi x0 y0 + phi x1 y1.
+// One more Shoup product than leaf2; same ranges.
+FCIRC_HD void leaf2_shift(uint32_t &a0, uint32_t &a1, uint32_t y0, uint32_t y1, Tw phi, uint32_t p,
+                          uint32_t p2, uint32_t pinv)
+{
+    const uint32_t x0 = canon4(a0, p, p2), x1 = canon4(a1, p, p2);
+    const uint32_t z0 = canon4(y0, p, p2), z1 = canon4(y1, p, p2);
+    const uint32_t x0f = reduce_once(shoup_mul(x0, phi.w, phi.wp, p), p);
+    const uint32_t x1f = reduce_once(shoup_mul(x1, phi.w, phi.wp, p), p);
+    const uint64_t t0 = (uint64_t)x1f * z0 + (uint64_t)x0 * z1;
+    const uint64_t t1 = (uint64_t)x0f * z0 + (uint64_t)x1f * z1;
+    a0 = redc(t0, p, pinv);
+    a1 = redc(t1, p, pinv);
+}
+
 }  // namespace fcirc

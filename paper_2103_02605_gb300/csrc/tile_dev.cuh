@@ -280,7 +280,10 @@ __device__ __forceinline__ void tile4096_dev(const TileJob &J, uint32_t N, uint3
     for (int q = 0; q < 8; ++q) {
         Tw phi = tc[3 + (q >> 1)];
         if (q & 1) phi = tw_neg(phi, p);
-        leaf2(a[2 * q], a[2 * q + 1], x[2 * q], x[2 * q + 1], phi, p, p2, pinv);
+        if constexpr (VAR == TILE_SHIFT)
+            leaf2_shift(a[2 * q], a[2 * q + 1], x[2 * q], x[2 * q + 1], phi, p, p2, pinv);
+        else
+            leaf2(a[2 * q], a[2 * q + 1], x[2 * q], x[2 * q + 1], phi, p, p2, pinv);
     }
     {
         const uint32_t *e8 = sg + 8 * 6, *e9 = sg + 9 * 6, *e10 = sg + 10 * 6;

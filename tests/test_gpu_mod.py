@@ -326,6 +326,34 @@ def test_poly_unaligned_inputs(F, orc):
     assert np.array_equal(C.cpu().numpy(), poly(F, Pc, Qc))
 
 
+def test_poly_output_alignments(F, orc):
+    """The output at offsets of 0 .. 3 int64 from a 32-byte boundary: the CRT
+    writes whole 32-byte quads only where they are aligned and otherwise
+    falls back to 8-byte stores; every placement gives the same product."""
+    import torch
+    n = 1 << 21
+    Pc, Qc = I.poly_pair(n, seed=I.SEED_BASE + 610, nq=n - 1)
+    dP, dQ = dev_u16(Pc), dev_u16(Qc)
+    buf = torch.full((2 * n + 8,), -1, dtype=torch.int64, device="cuda")
+    assert buf.data_ptr() % 32 == 0
+    ref = None
+    for off in (0, 1, 2, 3):
+        buf.fill_(-1)
+        out = buf[off:off + 2 * n - 2]
+        F.poly_mul_int(dP, dQ, out=out)
+        torch.cuda.synchronize()
+        B = buf.cpu().numpy()
+        assert (B[:off] == -1).all() and (B[off + 2 * n - 2:] == -1).all(), off   # nothing outside
+        C = B[off:off + 2 * n - 2]
+        if ref is None:
+            ref = C.copy()
+            idx = np.unique(np.concatenate([[0, 1, 2, 3, n - 1, n, 2 * n - 3],
+                                            np.random.default_rng(5).integers(0, 2 * n - 2, 40)])).astype(np.uint64)
+            assert np.array_equal(C[idx.astype(np.int64)], orc.poly_mul_coeffs(Pc, Qc, idx))
+        else:
+            assert np.array_equal(C, ref), off
+
+
 def test_poly_extreme_coefficients(F):
     n = 1 << 16
     Pc = np.full(n, 0xFFFF, np.uint16)
