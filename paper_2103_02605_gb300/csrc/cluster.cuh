@@ -7,6 +7,15 @@
 namespace fcirc {
 
 __device__ __forceinline__ void cl_arrive() { asm volatile("barrier.cluster.arrive.release.aligned;\n" ::: "memory"); }
+// Arrive without release semantics: for a thread whose only accesses the
+// peers wait on are distributed shared-memory loads whose values it has
+// already consumed (a load that fed a later instruction has completed).  It
+// does not wait for the thread's outstanding global stores, which the
+// release form does.
+__device__ __forceinline__ void cl_arrive_relaxed()
+{
+    asm volatile("barrier.cluster.arrive.relaxed.aligned;\n" ::: "memory");
+}
 __device__ __forceinline__ void cl_wait() { asm volatile("barrier.cluster.wait.acquire.aligned;\n" ::: "memory"); }
 __device__ __forceinline__ uint32_t cl_rank()
 {

@@ -160,6 +160,14 @@ __device__ __forceinline__ void grp_arrive()
 {
     if constexpr (CL > 1) cl_arrive();
 }
+// The arrive after a store phase: its only cross-CTA accesses were peer
+// shared-memory loads whose values its global stores consumed, so it needs no
+// release (which would wait for those stores to drain).
+template <int CL>
+__device__ __forceinline__ void grp_arrive_done()
+{
+    if constexpr (CL > 1) cl_arrive_relaxed();
+}
 template <int CL>
 __device__ __forceinline__ void grp_wait()
 {
@@ -445,7 +453,7 @@ __device__ __forceinline__ void c4fwd_jobs(const ColFwdParams &P, uint32_t *sm, 
         grp_arrive<Sh::CL>();
         grp_wait<Sh::CL>();
         c4_store_phase<LF>(sm, J.dst, base0, logS, rank, tid);
-        grp_arrive<Sh::CL>();
+        grp_arrive_done<Sh::CL>();
     }
     grp_wait<Sh::CL>();   // no CTA leaves while a peer still reads its shared memory
 }
@@ -572,6 +580,15 @@ __device__ __forceinline__ void crt_store4(const ColInvParams &P, uint32_t idx, 
     }
 }
 
+// Whether the quad of circulant entries idx .. idx+3 writes any coefficient.
+// The CRT loops load a quad's residues from the peers only when it does, so
+// every such load feeds a store before the closing relaxed arrive.
+__device__ __forceinline__ bool crt_quad_needed(const ColInvParams &P, uint32_t idx)
+{
+    if (idx < P.nout) return true;
+    return P.epi == EPI_CRT_ROT && ((idx + P.N - 1) & (P.N - 1)) < P.nout;
+}
+
 // CRT phase of the polynomial product: the rows of the store phase, the three
 // primes' canonical residues from the CTA that computed them, Garner's CRT,
 // and the int64 coefficients (crt_store4).
@@ -588,10 +605,12 @@ __device__ __forceinline__ void c4_crt_phase(const ColInvParams &P, const uint32
 #pragma unroll 2
     for (int k = 0; k < kC4Rows; ++k) {
         const int row = row_t + RSTEP * k;
+        const uint32_t idx = base0 + ((uint32_t)cq << 2) + ((uint32_t)row << logS);
+        if (!crt_quad_needed(P, idx)) continue;
         const uint4 r1 = c4_seg_ld<LF>(sb, cq, row);
         const uint4 r2 = c4_seg_ld<LF>(sb + PB, cq, row);
         const uint4 r3 = c4_seg_ld<LF>(sb + 2 * PB, cq, row);
-        crt_store4(P, base0 + ((uint32_t)cq << 2) + ((uint32_t)row << logS), r1, r2, r3);
+        crt_store4(P, idx, r1, r2, r3);
     }
 }
 
@@ -629,7 +648,7 @@ __global__ void __cluster_dims__(C4<LF>::CL, 1, 1) __launch_bounds__(kC4Threads,
         for (int q = 0; q < NP; ++q) c4_store_phase<LF>(sm + q * Sh::WORDS, P.job[q].dst, base0, logS, rank, tid);
     }
     // no CTA leaves while a peer still reads its shared memory
-    grp_arrive<Sh::CL>();
+    grp_arrive_done<Sh::CL>();
     grp_wait<Sh::CL>();
 }
 
@@ -674,12 +693,16 @@ __global__ void __cluster_dims__(3, 1, 1) __launch_bounds__(kC4Threads, 2)
 #pragma unroll 2
     for (int w = w0 + tid; w < w1; w += kC4Threads) {
         const int quad = w & ((1 << Sh::LNQ) - 1), row = w >> Sh::LNQ;
+        const uint32_t idx = base + ((uint32_t)quad << 2) + ((uint32_t)row << logS);
+        if (!crt_quad_needed(P, idx)) continue;
         const uint32_t off = 4u * (uint32_t)c4_off<LF>(quad, row);
         const uint4 r1 = cl_ld4(s1 + off), r2 = cl_ld4(s2 + off), r3 = cl_ld4(s3 + off);
-        crt_store4(P, base + ((uint32_t)quad << 2) + ((uint32_t)row << logS), r1, r2, r3);
+        crt_store4(P, idx, r1, r2, r3);
     }
-    cl_arrive();
-    cl_wait();   // no CTA leaves while a peer still reads its shared memory
+    // no CTA leaves while a peer still reads its shared memory (every peer
+    // load above fed a store: crt_quad_needed)
+    cl_arrive_relaxed();
+    cl_wait();
 }
 
 template <class K>
