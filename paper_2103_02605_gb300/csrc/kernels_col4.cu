@@ -272,6 +272,22 @@ __device__ __forceinline__ uint4 ld4_raw(const Src &s, uint32_t N, uint32_t idx)
     }
 }
 
+// Raw-source cache of the forward pass.  The jobs of a CTA that read one
+// uint16 source (the three primes of one side of a polynomial product) load
+// it from global memory once: the first job packs the 16-bit values of every
+// row it loads into shared memory behind the 64 KB exchange area, and the
+// others read them back there.  A thread reads only the slots it wrote (slot
+// k of thread t at word pair k * threads + t), so no barrier is needed, and the
+// cache replaces what would otherwise be re-reads through an L1 that the
+// scattered 8-byte row segments thrash.
+template <int MODE>
+struct C4Cache {
+    static constexpr bool ON = (MODE & 3) == SRC_U16 || (MODE & 3) == SRC_U16_REV;
+    static constexpr int ROWS = ((MODE >> 3) & 3) ? kC4Rows / 2 : kC4Rows;   // rows a thread loads
+    static constexpr int BYTES = ON ? ROWS * kC4Threads * 8 : 0;
+};
+enum : int { C4_NOCACHE = 0, C4_FILL = 1, C4_USE = 2 };
+
 // Twiddles of local level D of one group (slots 16 - 2^(D+1) .. 16 - 2^D of
 // its 16-entry block in the group-ordered table), in 64/128-bit loads.
 template <int D>
@@ -352,7 +368,8 @@ __device__ __forceinline__ uint4 get4(const uint32_t *v) { return make_uint4(v[0
 
 template <int LF, int S, int MODE, bool VEC>
 __device__ __forceinline__ void c4fwd_stage(const ColFwdJob &J, const ColFwdParams &P, uint32_t *sm,
-                                            uint32_t base, uint32_t pb, int logS, int tid, bool wait_first)
+                                            uint32_t base, uint32_t pb, int logS, int tid, bool wait_first,
+                                            int cache = C4_NOCACHE)
 {
     using Sh = C4<LF>;
     constexpr int NL = Sh::nl(S), D0 = Sh::d0(S);
@@ -372,7 +389,19 @@ __device__ __forceinline__ void c4fwd_stage(const ColFwdJob &J, const ColFwdPara
             if ((half == 1 && i < M / 2) || (half == 2 && i >= M / 2)) continue;
             const int row = row0 + (i << LST);
             uint4 w;
-            if constexpr (FIRST)
+            if constexpr (FIRST && C4Cache<MODE>::ON) {
+                // cache slot: the thread's k-th loaded row
+                constexpr int half_m = M / 2;
+                const int k = half ? hb * half_m + (i % half_m) : hb * M + i;
+                uint2 *rc = reinterpret_cast<uint2 *>(sm + C4<LF>::WORDS) + k * kC4Threads + tid;
+                if (cache == C4_USE) {
+                    const uint2 r = *rc;
+                    w = make_uint4(r.x & 0xFFFFu, r.x >> 16, r.y & 0xFFFFu, r.y >> 16);
+                } else {
+                    w = ld4_raw<MODE>(J.src, P.N, base + ((uint32_t)quad << 2) + ((uint32_t)row << logS));
+                    if (cache == C4_FILL) *rc = make_uint2(w.x | (w.y << 16), w.z | (w.w << 16));
+                }
+            } else if constexpr (FIRST)
                 w = ld4_raw<MODE>(J.src, P.N, base + ((uint32_t)quad << 2) + ((uint32_t)row << logS));
             else
                 w = *reinterpret_cast<const uint4 *>(sm + C4Addr<LF, LST>(quad, row0)(i));
@@ -434,10 +463,12 @@ __device__ __forceinline__ void c4fwd_jobs(const ColFwdParams &P, uint32_t *sm, 
     using Sh = C4<LF>;
     const int rank = Sh::CL > 1 ? (int)cl_rank() : 0;
     const uint32_t base0 = base - ((uint32_t)rank << (2 + Sh::LNQ));
+    const bool cached = C4Cache<MODE>::ON && P.share_src && P.jobs_per_cta > 1;
 #pragma unroll 1
     for (int jj = 0; jj < P.jobs_per_cta; ++jj) {
         const ColFwdJob &J = P.job[j0 + jj];
-        c4fwd_stage<LF, 0, MODE, VEC>(J, P, sm, base, pb, logS, tid, jj > 0);
+        c4fwd_stage<LF, 0, MODE, VEC>(J, P, sm, base, pb, logS, tid, jj > 0,
+                                      cached ? (jj == 0 ? C4_FILL : C4_USE) : C4_NOCACHE);
         if constexpr (Sh::NST > 1) {
             __syncthreads();
             c4fwd_stage<LF, 1, MODE, VEC>(J, P, sm, base, pb, logS, tid, false);
@@ -690,7 +721,7 @@ __global__ void __cluster_dims__(3, 1, 1) __launch_bounds__(kC4Threads, 2)
     const int w0 = q * W3, w1 = (q + 1) * W3 < W ? (q + 1) * W3 : W;
     const uint32_t own = smem_addr(sm);
     const uint32_t s1 = cl_map(own, 0), s2 = cl_map(own, 1), s3 = cl_map(own, 2);
-#pragma unroll 2
+#pragma unroll 4
     for (int w = w0 + tid; w < w1; w += kC4Threads) {
         const int quad = w & ((1 << Sh::LNQ) - 1), row = w >> Sh::LNQ;
         const uint32_t idx = base + ((uint32_t)quad << 2) + ((uint32_t)row << logS);
@@ -730,11 +761,18 @@ template <int LF, int M0, int M1>
 int launch_c4fwd_m(const ColFwdParams &P, int nctay, cudaStream_t s)
 {
     static std::atomic<unsigned> mask{0};
-    const int smem = C4<LF>::WORDS * 4;
-    FCIRC_TRY(c4_smem(k_colfwd4<LF, M0, M1>, smem, mask));
+    constexpr int cache_max = C4Cache<M0>::BYTES > C4Cache<M1>::BYTES ? C4Cache<M0>::BYTES : C4Cache<M1>::BYTES;
+    FCIRC_TRY(c4_smem(k_colfwd4<LF, M0, M1>, C4<LF>::WORDS * 4 + cache_max, mask));
     const uint64_t ncta = (uint64_t)1 << (P.l0 + (P.logn - P.l1) - 2 - C4<LF>::LNQ);
     // optionally one job per CTA (more, shorter CTAs)
     ColFwdParams P1 = P;
+    // the raw-source cache serves job groups whose jobs all read one source
+    P1.share_src = 1;
+    for (int k = 0; k < nctay * P.jobs_per_cta; ++k) {
+        const Src &a = P.job[k].src, &b = P.job[(k / P.jobs_per_cta) * P.jobs_per_cta].src;
+        if (a.ptr != b.ptr || a.len != b.len || a.kind != b.kind) P1.share_src = 0;
+    }
+    const int smem = C4<LF>::WORDS * 4 + (P1.share_src && P.jobs_per_cta > 1 ? cache_max : 0);
     int ny = nctay;
     if (FCIRC_C4_SPLITJOBS) {
         ny = nctay * P.jobs_per_cta;

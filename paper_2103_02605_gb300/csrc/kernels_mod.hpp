@@ -137,6 +137,7 @@ struct ColFwdParams {
     ColFwdJob job[6];
     int jobs_per_cta;      // 1, or 3 for the three primes of one side of a product
     int vec_group0;        // job groups [0, vec_group0) are row-vector side (set by the launcher)
+    int share_src;         // every job group reads one source (set by the launcher)
     uint32_t N;
     int logn, l0, l1;
     int stage_off[3];
