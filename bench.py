@@ -257,9 +257,9 @@ _KSRC = {
     "k_tile4096": ["kernels_tile.cu", "tile_dev.cuh", "modarith.cuh", "kernels_mod.hpp"],
 }
 NCU_TRAFFIC = {
-    "k_colfwd4": (381241856, "cbbe4ba1e63f3b30"),
-    "k_tile4096": (563171584, "58676623955ca72c"),
-    "k_colinv4x3": (308362752, "cbbe4ba1e63f3b30"),
+    "k_colfwd4": (381384960, "cb18a18fbb281a9d"),
+    "k_tile4096": (563373824, "ab82d8047edfca31"),
+    "k_colinv4x3": (304268544, "cb18a18fbb281a9d"),
 }
 
 
