@@ -38,62 +38,52 @@ __device__ __forceinline__ SsaTw<W> cneg(SsaTw<W> t)
     return SsaTw<W>{t.e >= K ? t.e - K : t.e + K};
 }
 
-// The value t = lo + hi 2^K, lo < 2^K, hi in [-3, 3], reduced into [0, 2^K]:
-// first lo - hi as words and a signed top in {-1, 0, 1}, then one correction
-// by 2^K + 1 (2^K = -1).
+// The value t = lo + hi 2^K, lo < 2^K, hi in [-3, 3], reduced into [0, 2^K],
+// without data-dependent branches (the lanes of a warp hold different
+// elements, so a branch here would split the warp).  2^K = -1, so
+// t = lo - hi: first r = lo - hi as W words and a signed top e in
+// {-1, 0, 1}, so t = r - e (mod 2^K + 1); then r - e as W words again, whose
+// carry out decides the one case that lands on 2^K itself.
 template <int W>
 __device__ __forceinline__ SsaE<W> ssa_norm(const uint64_t *lo, int hi)
 {
-    SsaE<W> r;
-    int ext = 0;
-    if (hi >= 0) {
-        uint64_t b = (uint64_t)hi;
+    // r = lo + c with c = -hi sign-extended over W words
+    const int64_t c = -(int64_t)hi;
+    const uint64_t ext = c < 0 ? ~0ull : 0ull;
+    uint64_t r[W], carry = 0;
 #pragma unroll
-        for (int i = 0; i < W; ++i) {
-            const uint64_t v = lo[i];
-            r.w[i] = v - b;
-            b = v < b ? 1u : 0u;
-        }
-        ext = -(int)b;
-    } else {
-        uint64_t c = (uint64_t)(-hi);
-#pragma unroll
-        for (int i = 0; i < W; ++i) {
-            const uint64_t v = lo[i] + c;
-            c = v < c ? 1u : 0u;
-            r.w[i] = v;
-        }
-        ext = (int)c;
+    for (int i = 0; i < W; ++i) {
+        const uint64_t add = i == 0 ? (uint64_t)c : ext;
+        const uint64_t t = lo[i] + add;
+        const uint64_t c1 = t < add ? 1u : 0u;
+        r[i] = t + carry;
+        carry = c1 + (r[i] < t ? 1u : 0u);
     }
-    r.top = 0;
-    if (ext < 0) {
-        // t + 2^K + 1 = words + 1, in [2^K - 2, 2^K]
-        uint64_t c = 1;
+    // the W-word sum with the sign extension: top word e = carry + ext
+    const int e = (int)(carry & 1u) - (c < 0 ? 1 : 0);
+    // value = r - e; d = -e in {-1, 0, 1} added the same way
+    const int64_t d = -(int64_t)e;
+    const uint64_t dext = d < 0 ? ~0ull : 0ull;
+    SsaE<W> o;
+    carry = 0;
 #pragma unroll
-        for (int i = 0; i < W; ++i) {
-            const uint64_t v = r.w[i] + c;
-            c = v < c ? 1u : 0u;
-            r.w[i] = v;
-        }
-        r.top = c;   // words wrapped to 0: the value is 2^K
-    } else if (ext > 0) {
-        // t = 2^K + words, words <= 2: 2^K itself, or words - 1
-        bool zero = true;
-#pragma unroll
-        for (int i = 0; i < W; ++i) zero = zero && r.w[i] == 0;
-        if (zero) {
-            r.top = 1;
-        } else {
-            uint64_t b = 1;
-#pragma unroll
-            for (int i = 0; i < W; ++i) {
-                const uint64_t v = r.w[i];
-                r.w[i] = v - b;
-                b = v < b ? 1u : 0u;
-            }
-        }
+    for (int i = 0; i < W; ++i) {
+        const uint64_t add = i == 0 ? (uint64_t)d : dext;
+        const uint64_t t = r[i] + add;
+        const uint64_t c1 = t < add ? 1u : 0u;
+        o.w[i] = t + carry;
+        carry = c1 + (o.w[i] < t ? 1u : 0u);
     }
-    return r;
+    carry &= 1u;
+    // d = +1: a carry out means r was 2^K - 1 and the words wrapped to 0 --
+    //         the value 2^K;
+    // d = -1: no carry out means r was 0 (a borrow) -- again 2^K, words 0.
+    const bool up = d > 0 && carry;
+    const bool down = d < 0 && !carry;
+#pragma unroll
+    for (int i = 0; i < W; ++i) o.w[i] = down ? 0ull : o.w[i];
+    o.top = (up || down) ? 1u : 0u;
+    return o;
 }
 
 template <int W>
@@ -141,53 +131,48 @@ __device__ __forceinline__ SsaE<W> cneg(SsaE<W> a)
     return csub<W>(ssa_zero<W>(), a);
 }
 
-// x 2^e for 0 <= e < K, x < 2^K: the 2W-word shift split at bit K into
-// lo - hi (2^K = -1).
-template <int W>
-__device__ __forceinline__ SsaE<W> ssa_shift_low(const SsaE<W> &x, int e)
-{
-    const int q = e >> 6, s = e & 63;
-    uint64_t sh[2 * W];
-#pragma unroll
-    for (int j = 0; j < 2 * W; ++j) sh[j] = 0;
-#pragma unroll
-    for (int qq = 0; qq < W; ++qq) {
-        if (q == qq) {
-#pragma unroll
-            for (int i = 0; i < W; ++i) {
-                sh[i + qq] |= s ? (x.w[i] << s) : x.w[i];
-                if (s && i + qq + 1 < 2 * W) sh[i + qq + 1] |= x.w[i] >> (64 - s);
-            }
-        }
-    }
-    SsaE<W> lo, hi;
-#pragma unroll
-    for (int i = 0; i < W; ++i) {
-        lo.w[i] = sh[i];
-        hi.w[i] = sh[W + i];
-    }
-    lo.top = hi.top = 0;
-    return csub<W>(lo, hi);
-}
+// v >> (64 - s) for 0 <= s < 64, 0 when s = 0, without a branch
+__device__ __forceinline__ uint64_t ssa_rsh_c(uint64_t v, int s) { return (v >> 1) >> (63 - s); }
 
-// twiddle product x 2^e, 0 <= e < 2K
+// twiddle product x 2^e, 0 <= e < 2K.  With e = e' + K [e >= K] (2^K = -1),
+// x 2^e' is the 2W-word shift of x split at bit K into lo - hi, and the
+// factor -1 swaps the operands of that subtraction.  The element 2^K
+// (top = 1, words 0) contributes 2^(K + e'): the bit e' of hi.  One
+// subtraction, no branch.
 template <int W>
 __device__ __forceinline__ SsaE<W> cmul(SsaTw<W> t, SsaE<W> x)
 {
     constexpr int K = 64 * W;
     const bool negate = t.e >= K;
     const int e = negate ? t.e - K : t.e;
-    SsaE<W> r;
-    if (x.top) {
-        // 2^K 2^e = -2^e
-        SsaE<W> p = ssa_zero<W>();
+    const int q = e >> 6, s = e & 63;
+    uint64_t sh[2 * W];
 #pragma unroll
-        for (int i = 0; i < W; ++i) p.w[i] = (e >> 6) == i ? (uint64_t)1 << (e & 63) : 0u;
-        r = cneg<W>(p);
-    } else {
-        r = ssa_shift_low<W>(x, e);
+    for (int j = 0; j < 2 * W; ++j) sh[j] = 0;
+#pragma unroll
+    for (int qq = 0; qq < W; ++qq) {
+        const uint64_t m = q == qq ? ~0ull : 0ull;
+#pragma unroll
+        for (int i = 0; i < W; ++i) {
+            sh[i + qq] |= (x.w[i] << s) & m;
+            if (i + qq + 1 < 2 * W) sh[i + qq + 1] |= ssa_rsh_c(x.w[i], s) & m;
+        }
     }
-    return negate ? cneg<W>(r) : r;
+    SsaE<W> lo, hi;
+#pragma unroll
+    for (int i = 0; i < W; ++i) {
+        lo.w[i] = sh[i];
+        hi.w[i] = sh[W + i] | ((x.top && q == i) ? (1ull << s) : 0ull);
+    }
+    lo.top = hi.top = 0;
+    SsaE<W> u, v;
+#pragma unroll
+    for (int i = 0; i < W; ++i) {
+        u.w[i] = negate ? hi.w[i] : lo.w[i];
+        v.w[i] = negate ? lo.w[i] : hi.w[i];
+    }
+    u.top = v.top = 0;
+    return csub<W>(u, v);
 }
 
 template <int W>
@@ -196,13 +181,13 @@ __device__ __forceinline__ SsaE<W> cmul(SsaE<W> x, SsaTw<W> t)
     return cmul<W>(t, x);
 }
 
-// general product (the leaves): the 2W-word schoolbook product split at bit
-// K into lo - hi; an operand 2^K = -1 negates the other
+// general product (the leaves): the 2W-word schoolbook product of the words
+// split at bit K into lo - hi, then the element 2^K = -1 handled by one more
+// subtraction, without a branch: a.top = 1 (a.w = 0) makes the word product
+// 0 and the result -b; b.top = 1 alone gives -a; both give -(2^K) = 1.
 template <int W>
 __device__ __forceinline__ SsaE<W> cmul(SsaE<W> a, SsaE<W> b)
 {
-    if (a.top) return cneg<W>(b);
-    if (b.top) return cneg<W>(a);
     uint64_t p[2 * W];
 #pragma unroll
     for (int j = 0; j < 2 * W; ++j) p[j] = 0;
@@ -228,7 +213,13 @@ __device__ __forceinline__ SsaE<W> cmul(SsaE<W> a, SsaE<W> b)
         hi.w[i] = p[W + i];
     }
     lo.top = hi.top = 0;
-    return csub<W>(lo, hi);
+    const SsaE<W> r = csub<W>(lo, hi);
+    // the top terms: -b when a = 2^K, -a when b = 2^K (r is 0 then)
+    SsaE<W> m;
+#pragma unroll
+    for (int i = 0; i < W; ++i) m.w[i] = a.top ? b.w[i] : (b.top ? a.w[i] : 0ull);
+    m.top = a.top ? b.top : 0u;
+    return csub<W>(r, m);
 }
 
 }  // namespace fcirc
