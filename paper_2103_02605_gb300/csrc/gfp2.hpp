@@ -10,7 +10,7 @@
 #pragma once
 #include <stdint.h>
 
-#include "modarith.cuh"   // FCIRC_HD
+#include "modarith.cuh"   // FCIRC_HD, reduce_min
 
 namespace fcirc {
 namespace gf {
@@ -22,24 +22,30 @@ struct E {
 };
 
 // x mod p for any 64-bit x (two folds of 2^31 = 1, one subtraction)
+// x mod p for x < 2^63, in 32-bit words (2^31 = 1 mod p): with
+// x = lo + 2^31 h, h = x >> 31 < 2^32 is first folded to h' = (h & p) +
+// (h >> 31) <= 2^31, so that lo + h' <= p + 2^31 = 2^32 - 1 does not
+// overflow; one more fold leaves t <= p + 1, and one add-and-min
+// (reduce_min) makes it canonical.
 FCIRC_HD uint32_t red(uint64_t x)
 {
-    x = (x & P) + (x >> 31);   // < 2^31 + 2^33
-    x = (x & P) + (x >> 31);   // < 2^31 + 8
-    return (uint32_t)(x >= P ? x - P : x);
+    const uint32_t lo = (uint32_t)x & P;
+    uint32_t h = (uint32_t)(x >> 31);
+    h = (h & P) + (h >> 31);                    // <= 2^31
+    const uint32_t s = lo + h;                  // <= 2^32 - 1
+    const uint32_t t = (s & P) + (s >> 31);     // <= p + 1
+    return reduce_min(t, P);
 }
 
-FCIRC_HD uint32_t add1(uint32_t a, uint32_t b)
-{
-    const uint32_t s = a + b;   // < 2^32
-    return s >= P ? s - P : s;
-}
+// a + b for canonical a, b (the sum is below 2p < 2^32)
+FCIRC_HD uint32_t add1(uint32_t a, uint32_t b) { return reduce_min(a + b, P); }
 
 FCIRC_HD uint32_t sub1(uint32_t a, uint32_t b) { return add1(a, P - b); }
 
 FCIRC_HD E add(E a, E b) { return E{add1(a.re, b.re), add1(a.im, b.im)}; }
 FCIRC_HD E sub(E a, E b) { return E{sub1(a.re, b.re), sub1(a.im, b.im)}; }
-FCIRC_HD E neg(E a) { return E{a.re ? P - a.re : 0u, a.im ? P - a.im : 0u}; }
+// p - a, with p itself (a = 0) reduced to 0
+FCIRC_HD E neg(E a) { return E{reduce_min(P - a.re, P), reduce_min(P - a.im, P)}; }
 
 // (a + b s)(c + d s) = (ac + 3 bd) + (ad + bc) s, s = sqrt 3
 FCIRC_HD E mul(E a, E b)
