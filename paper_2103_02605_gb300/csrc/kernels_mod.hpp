@@ -41,7 +41,7 @@ struct TileJob {
 // in [0, 4p)) for reuse with many vectors.  TILE_PLANNED: J.a is such a
 // transformed row vector (read as it is); the vector tree, the leaves and
 // the recombination.  TILE_SHIFT: TILE_FULL with the row vector shifted by
-// one place in the leaves (leaf2_shift), which moves the product up by one
+// one place in the leaves (bfly_rec_shift), which moves the product up by one
 // entry when f = 1: the polynomial product's reversed-row embedding then
 // needs no rotation of its output.
 enum : int { TILE_FULL = 0, TILE_ROW = 1, TILE_PLANNED = 2, TILE_SHIFT = 3 };

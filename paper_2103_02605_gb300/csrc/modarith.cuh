@@ -161,6 +161,23 @@ FCIRC_HD void bfly_rec(uint32_t &m1, uint32_t &m2, Tw si, uint32_t p, uint32_t p
     m2 = reduce_once(d, p2);                       // [0, 2p)
 }
 
+// Row vector shifted by one place (a'_k = a_(k-1), indices mod n; at f = 1
+// the product's entries move up by one, c'_i = c_(i+1)).  The shift is
+// z a(z), so a 2x2 leaf's row (x0, x1) = a mod (z^2 - phi) becomes
+// (phi x1, x0), and the leaf gives c'_0 = c1 and c'_1 = phi c0, with (c0, c1)
+// what leaf2 gives for the unshifted row.  The factor phi = +-s costs no
+// multiplication when it is left to the first recombination level: the
+// position-1 entries of sibling leaves, s c0_A and -s c0_B, recombine as
+// (c0_A - c0_B, s (c0_A + c0_B)).  bfly_rec_shift is that butterfly; it
+// takes the forward twiddle s.  In (0, 2p), out [0, 2p).
+FCIRC_HD void bfly_rec_shift(uint32_t &m1, uint32_t &m2, Tw s, uint32_t p, uint32_t p2)
+{
+    const uint32_t sum = m1 + m2;                  // (0, 4p)
+    const uint32_t d = m1 - m2 + p2;               // (0, 4p)
+    m1 = reduce_once(d, p2);                       // [0, 2p)
+    m2 = shoup_mul(sum, s.w, s.wp, p);             // [0, 2p)
+}
+
 // 2x2 leaf: the phi-circulant [[a0, a1], [phi a1, a0]] times (y0, y1) --
 // Definition 2 at n = 2, which is what Algorithm 1 gives for 1x1 blocks.
 // Each output is one 64-bit sum of two products of canonical residues
@@ -176,25 +193,6 @@ FCIRC_HD void leaf2(uint32_t &a0, uint32_t &a1, uint32_t y0, uint32_t y1, Tw phi
     const uint32_t x1f = reduce_once(shoup_mul(x1, phi.w, phi.wp, p), p);
     const uint64_t t0 = (uint64_t)x0 * z0 + (uint64_t)x1 * z1;
     const uint64_t t1 = (uint64_t)x1f * z0 + (uint64_t)x0 * z1;
-    a0 = redc(t0, p, pinv);
-    a1 = redc(t1, p, pinv);
-}
-
-// The same leaf for the row vector shifted by one place (a'_k = a_(k-1),
-// indices mod n; the product's entries move up by one, c'_i = c_(i+1), when
-// the root parameter is 1).  The shift is z a(z), so the leaf's row
-// (x0, x1) = a mod (z^2 - phi) becomes (phi x1, x0):
-//   c'_0 = phi x1 y0 + x0 y1,   c'_1 = phi x0 y0 + phi x1 y1.
-// One more Shoup product than leaf2; same ranges.
-FCIRC_HD void leaf2_shift(uint32_t &a0, uint32_t &a1, uint32_t y0, uint32_t y1, Tw phi, uint32_t p,
-                          uint32_t p2, uint32_t pinv)
-{
-    const uint32_t x0 = canon4(a0, p, p2), x1 = canon4(a1, p, p2);
-    const uint32_t z0 = canon4(y0, p, p2), z1 = canon4(y1, p, p2);
-    const uint32_t x0f = reduce_once(shoup_mul(x0, phi.w, phi.wp, p), p);
-    const uint32_t x1f = reduce_once(shoup_mul(x1, phi.w, phi.wp, p), p);
-    const uint64_t t0 = (uint64_t)x1f * z0 + (uint64_t)x0 * z1;
-    const uint64_t t1 = (uint64_t)x0f * z0 + (uint64_t)x1f * z1;
     a0 = redc(t0, p, pinv);
     a1 = redc(t1, p, pinv);
 }

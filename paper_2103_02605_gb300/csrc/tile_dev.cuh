@@ -280,10 +280,20 @@ __device__ __forceinline__ void tile4096_dev(const TileJob &J, uint32_t N, uint3
     for (int q = 0; q < 8; ++q) {
         Tw phi = tc[3 + (q >> 1)];
         if (q & 1) phi = tw_neg(phi, p);
-        if constexpr (VAR == TILE_SHIFT)
-            leaf2_shift(a[2 * q], a[2 * q + 1], x[2 * q], x[2 * q + 1], phi, p, p2, pinv);
-        else
-            leaf2(a[2 * q], a[2 * q + 1], x[2 * q], x[2 * q + 1], phi, p, p2, pinv);
+        leaf2(a[2 * q], a[2 * q + 1], x[2 * q], x[2 * q + 1], phi, p, p2, pinv);
+        if constexpr (VAR == TILE_SHIFT) {
+            // the row vector shifted by one place (bfly_rec_shift): entry 0
+            // is c1, entry 1 is phi c0 -- kept as c0 here, the factor phi
+            // going into the first recombination level
+            const uint32_t c0 = a[2 * q];
+            a[2 * q] = a[2 * q + 1];
+            a[2 * q + 1] = c0;
+        }
+    }
+    Tw f10[4];   // forward level-10 twiddles, for bfly_rec_shift
+    if constexpr (VAR == TILE_SHIFT) {
+#pragma unroll
+        for (int r = 0; r < 4; ++r) f10[r] = tc[3 + r];
     }
     {
         const uint32_t *e8 = sg + 8 * 6, *e9 = sg + 9 * 6, *e10 = sg + 10 * 6;
@@ -293,7 +303,18 @@ __device__ __forceinline__ void tile4096_dev(const TileJob &J, uint32_t N, uint3
 #pragma unroll
         for (int r = 0; r < 4; ++r) tc[3 + r] = twiddle_from(J.Ui[1024 + 4 * tid + r], e10[3], e10[4], e10[5], p);
     }
-    rec1<4, 3>(a, [&](int d, int j) { return tc[(1 << d) - 1 + j]; }, p, p2);
+    if constexpr (VAR == TILE_SHIFT) {
+        // level 10: position-0 pairs as usual, position-1 pairs with the
+        // leaves' missing factor phi = +-s
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            bfly_rec(a[4 * j], a[4 * j + 2], tc[3 + j], p, p2);
+            bfly_rec_shift(a[4 * j + 1], a[4 * j + 3], f10[j], p, p2);
+        }
+        rec1<4, 2>(a, [&](int d, int j) { return tc[(1 << d) - 1 + j]; }, p, p2);
+    } else {
+        rec1<4, 3>(a, [&](int d, int j) { return tc[(1 << d) - 1 + j]; }, p, p2);
+    }
     __syncthreads();
 #pragma unroll
     for (int q = 0; q < 4; ++q)
