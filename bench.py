@@ -411,13 +411,12 @@ def run_extras(F, I, dev, stream):
     return out
 
 
-# Kernels that only the secondary workloads launch, by the library's trace
-# names (the planned tile is k_tile4096<0, 0, 2>), profiled by
-#   ncu --set full --clock-control none --kernel-name-base demangled
-#       -k regex:"k_tile4096<0, 0, 2>|k_cfwd|k_cbwd|k_bmain|k_gfwd|k_sfwd"
-#       -s M -c M python bench.py --profile-extras
-# with M the launches of one round that --profile-extras prints.
-PROFILE_EXTRA_KERNELS = "k_tile4096_planned|k_cfwd|k_cbwd|k_bmain|k_gfwd|k_sfwd"
+# Kernels that only the secondary workloads launch (by the prefix of the
+# library's trace names, which the CUDA function names share), profiled by
+#   ncu --set full --clock-control none -k regex:"<PROFILE_EXTRA_KERNELS>"
+#       -s SKIP -c COUNT python bench.py --profile-extras
+# with SKIP and COUNT as --profile-extras prints them.
+PROFILE_EXTRA_KERNELS = "k_tile4096|k_cfwd|k_cbwd|k_bmain|k_gfwd|k_sfwd"
 
 
 def profile_extras(F, I, dev, stream):
@@ -425,16 +424,26 @@ def profile_extras(F, I, dev, stream):
     a warm-up), on the inputs run_extras times: the fixed-matrix plan's
     product at n = 2^24, the complex layer 4096 x 2^10 forward + backward,
     10,000 uneven batched instances in one graph launch, GF(p^2) 10,000 x
-    2048 and Z/(2^128 + 1) 20,000 x 256.  Prints how many launches of
-    PROFILE_EXTRA_KERNELS one round makes (ncu's skip and count)."""
+    2048 and Z/(2^128 + 1) 20,000 x 256.  Prints ncu's skip (the launches
+    of PROFILE_EXTRA_KERNELS before the second round) and count (one
+    round's)."""
+    import re
     import numpy as np
     import torch
+    pat = re.compile(PROFILE_EXTRA_KERNELS)
+
+    def matches(rep):
+        return sum(c for k, (c, _) in rep.items() if pat.match(k))
     n = 1 << 24
     a, x = I.single_mod(n, seed=I.SEED_BASE + 10)
     da = torch.from_numpy(a.view(np.int32)).to(dev)
     dx = torch.from_numpy(x.view(np.int32)).to(dev)
     dc = torch.empty_like(da)
-    plan = F.APlan(I.P1, 1, da, stream=stream)
+    F.prof_start()
+    plan = F.APlan(I.P1, 1, da, stream=stream)   # its row-vector tile runs here
+    torch.cuda.synchronize()
+    F.prof_stop()
+    setup = matches(F.prof_report())
     ca, cx, cg = (torch.from_numpy(v).to(dev) for v in I.complex_layer(4096, 1024))
     nn, f, off, ba, bx = I.batched_mod()
     bf = torch.from_numpy(f.view(np.int32)).to(dev)
@@ -458,8 +467,6 @@ def profile_extras(F, I, dev, stream):
              lambda: graph.launch(stream=stream),
              lambda: F.fcirc_matvec_gf(ga, gx, (1, 0), stream=stream),
              lambda: F.fcirc_matvec_ssa(sa, sx, 128, 128, stream=stream)]
-    import re
-    pat = re.compile(PROFILE_EXTRA_KERNELS)
     for rnd in range(2):
         F.prof_start()
         for c in calls:
@@ -468,10 +475,10 @@ def profile_extras(F, I, dev, stream):
         F.prof_stop()
         rep = F.prof_report()
     # the graph's k_bmain is not traced (graph replay): one launch per round
-    per_round = sum(c for k, (c, _) in rep.items() if pat.fullmatch(k)) + 1
+    per_round = matches(rep) + 1
     graph.destroy()
     plan.destroy()
-    print(f"PROFILE_EXTRA_MATCHES_PER_ROUND={per_round}", flush=True)
+    print(f"PROFILE_EXTRA_SKIP={setup + per_round} PROFILE_EXTRA_COUNT={per_round}", flush=True)
     return 0
 
 
