@@ -257,9 +257,9 @@ _KSRC = {
     "k_tile4096": ["kernels_tile.cu", "tile_dev.cuh", "modarith.cuh", "kernels_mod.hpp"],
 }
 NCU_TRAFFIC = {
-    "k_colfwd4": (381384960, "cb18a18fbb281a9d"),
-    "k_tile4096": (563373824, "ab82d8047edfca31"),
-    "k_colinv4x3": (304268544, "cb18a18fbb281a9d"),
+    "k_colfwd4": (381068800, "ab72dc9ac4948ba2"),
+    "k_tile4096": (563151104, "dd14cbf1e61a1982"),
+    "k_colinv4x3": (304178944, "ab72dc9ac4948ba2"),
 }
 
 
