@@ -299,6 +299,34 @@ def _time(fn, reps, flush, stream, warm=2):
     return statistics.median(ts), min(ts)
 
 
+def _extra_roofline(ms, elems, slots_per_elem=None, bytes_per_elem=None, flops_per_elem=None, bound=None):
+    """Roofline fractions of one secondary workload from its median time:
+    algorithmic multiply slots (the headline's unit: a Shoup product is 4,
+    so a butterfly is 2 per element and level), compulsory HBM bytes and
+    FP32 flops per element, each against the measured peak (HBM) or the
+    unit count x the measured maximum SM clock (multiply pipe: 152 SMs x 64
+    slots per cycle; FP32: 152 SMs x 128 lanes x 2 flops per cycle)."""
+    peaks, kind = measured_peaks()
+    mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    sec = ms * 1e-3
+    r = {"peak_source": kind}
+    if bound:
+        r["bound"] = bound
+    if slots_per_elem is not None:
+        ach = slots_per_elem * elems / sec / 1e12
+        pk = N_SMS * SLOTS_PER_SM_CYCLE * mhz * 1e6 / 1e12
+        r["mul_slots"] = {"per_elem": slots_per_elem, "achieved_tslots": ach, "peak_tslots": pk, "frac": ach / pk}
+    if flops_per_elem is not None:
+        ach = flops_per_elem * elems / sec / 1e12
+        pk = N_SMS * 128 * 2 * mhz * 1e6 / 1e12
+        r["fp32"] = {"per_elem": flops_per_elem, "achieved_tflops": ach, "peak_tflops": pk, "frac": ach / pk}
+    if bytes_per_elem is not None:
+        ach = bytes_per_elem * elems / sec / 1e9
+        r["hbm"] = {"bytes_per_elem": bytes_per_elem, "achieved_gbs": ach, "peak_gbs": float(peaks["hbm_gbs"]),
+                    "frac": ach / float(peaks["hbm_gbs"])}
+    return r
+
+
 def run_extras(F, I, dev, stream):
     """The other workloads of the method, each on its own inputs: single
     products, products with a fixed-matrix plan against plain ones, the
@@ -408,6 +436,40 @@ def run_extras(F, I, dev, stream):
     to = torch.empty(A.size + B.size, dtype=torch.int16, device=dev)
     med, mn = _time(lambda: F.bigint_mul(tA, tB, out=to, stream=stream), 10, flush, stream)
     out["bigint_2^26bit"] = {"ms": med, "ms_min": mn, "Glimb_s": (A.size + B.size) / (med * 1e-3) / 1e9}
+
+    # roofline fractions (algorithmic counts per element; see _extra_roofline):
+    #  * f-circulant products mod p, n = 2^24: 3 trees x 23 levels x 2 slots;
+    #    the transposed product adds one Shoup product (4 slots) per element,
+    #    the fixed-matrix product runs 2 trees; 12 bytes (a, x in, c out);
+    #  * batched: 3 trees x (log2 n_i - 1) levels x 2 slots per residue,
+    #    12 bytes;
+    #  * complex layer: 3 products (forward; both gradients) of 3 trees x 9
+    #    levels x 5 flops (a complex product and two sums per butterfly of two
+    #    numbers) plus 17 flops per number at the 2x2 leaves; 64 bytes
+    #    (24 forward, 40 backward);
+    #  * GF(p^2) and Z/(2^128 + 1): bound by the ALU pipe (ncu), whose work
+    #    has no multiply-slot count; their compulsory bytes: 3 elements of 8
+    #    and of 24 bytes;
+    #  * large integers, 2^26 x 2^26 bits (circulant N = 2^23, 3 primes):
+    #    3 primes x 3 trees x 22 levels x 2 slots + 21 for the CRT per
+    #    circulant element; 2 bytes in per input limb, 2 out per product limb.
+    n24 = 1 << 24
+    out["fcirc_matvec_n2^24"]["roofline"] = _extra_roofline(out["fcirc_matvec_n2^24"]["ms"], n24, 138, 12)
+    out["fcirc_matvec_t_n2^24"]["roofline"] = _extra_roofline(out["fcirc_matvec_t_n2^24"]["ms"], n24, 142, 12)
+    out["fcirc_matvec_aplan_n2^24"]["roofline"] = _extra_roofline(out["fcirc_matvec_aplan_n2^24"]["ms"], n24, 92, 12)
+    tot = float(np.sum(nn.astype(np.float64)))
+    bslots = float(np.sum(nn.astype(np.float64) * 6 * (np.log2(nn.astype(np.float64)) - 1))) / tot
+    out["batched_10000_uneven"]["roofline"] = _extra_roofline(out["batched_10000_uneven"]["graph_ms"], tot,
+                                                              bslots, 12)
+    out["complex_fwd_bwd_4096x1024"]["roofline"] = _extra_roofline(out["complex_fwd_bwd_4096x1024"]["fused_ms"],
+                                                                   4096 * 1024, None, 64, 3 * (3 * 9 * 5 + 17),
+                                                                   bound="shared-memory bandwidth (ncu)")
+    out["gfp2_10000x2048"]["roofline"] = _extra_roofline(out["gfp2_10000x2048"]["ms"], 10000 * 2048, None, 24,
+                                                         bound="alu (ncu)")
+    out["ssa_K128_20000x256"]["roofline"] = _extra_roofline(out["ssa_K128_20000x256"]["ms"], 20000 * 256, None, 72,
+                                                            bound="alu (ncu)")
+    out["bigint_2^26bit"]["roofline"] = _extra_roofline(out["bigint_2^26bit"]["ms"], 1 << 23,
+                                                        3 * 3 * 22 * 2 + 21, (A.size + B.size) * 4 / (1 << 23))
     return out
 
 
