@@ -25,7 +25,10 @@
 //    vector, read in source mode M0; 1: vector, mode M1).
 //  * k_colinv4<LF, NP>: the recombination levels; with NP = 3 the three
 //    primes of a polynomial product stay in shared memory and a CRT phase
-//    writes the rotated int64 coefficients.
+//    writes the int64 coefficients (crt_store4).
+//  * k_colinv4x3<LF>: the polynomial product's last pass, one prime per CTA
+//    of a three-CTA cluster, the CRT gathered through distributed shared
+//    memory.
 //
 // Inputs need 16-byte (uint32 sources) or 8-byte (uint16 sources) aligned
 // pointers; the launchers check that and otherwise leave the pass to the
