@@ -19,6 +19,7 @@ from __future__ import annotations
 
 import argparse
 import json
+import re
 import os
 import statistics
 import subprocess
@@ -248,8 +249,9 @@ def kernel_bytes():
 
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) per launch of
 # each kernel from one ncu capture of this workload, with the digest of the
-# source files that define the kernel when it was taken; once one of them
-# changes the figure is stale and the bench reports null.  The summaries in
+# code (comments aside) of the source files that define the kernel when it
+# was taken; once that code changes the figure is stale and the bench
+# reports null.  The summaries in
 # profiles/ give the commands and the other counters.
 _KSRC = {
     "k_colfwd4": ["kernels_col4.cu", "cluster.cuh", "tile_dev.cuh", "modarith.cuh", "kernels_mod.hpp"],
@@ -257,20 +259,32 @@ _KSRC = {
     "k_tile4096": ["kernels_tile.cu", "tile_dev.cuh", "modarith.cuh", "kernels_mod.hpp"],
 }
 NCU_TRAFFIC = {
-    "k_colfwd4": (381068800, "ab72dc9ac4948ba2"),
-    "k_tile4096": (563151104, "dd14cbf1e61a1982"),
-    "k_colinv4x3": (304178944, "ab72dc9ac4948ba2"),
+    "k_colfwd4": (381068800, "0b6340b27c0e0bb3"),
+    "k_tile4096": (563151104, "33925eae45968c44"),
+    "k_colinv4x3": (304178944, "0b6340b27c0e0bb3"),
 }
 
 
+_CODE_TOKENS = re.compile(r'//[^\n]*|/\*.*?\*/|"(?:\\.|[^"\\])*"|\'(?:\\.|[^\'\\])*\'', re.S)
+
+
+def code_only(text):
+    """C/C++ source without comments, whitespace collapsed: the part of a
+    file that decides the compiled kernel."""
+    text = _CODE_TOKENS.sub(lambda m: " " if m.group(0).startswith("/") else m.group(0), text)
+    return " ".join(text.split())
+
+
 def kernel_source_digest(kernel):
+    """Digest of the code (comments and layout aside) of the files that
+    define `kernel`."""
     import hashlib
     d = os.path.join(ROOT, "paper_2103_02605_gb300", "csrc")
     h = hashlib.sha256()
     for name in _KSRC.get(kernel, sorted(os.listdir(d))):
         h.update(name.encode())
-        with open(os.path.join(d, name), "rb") as fh:
-            h.update(fh.read())
+        with open(os.path.join(d, name), encoding="utf-8") as fh:
+            h.update(code_only(fh.read()).encode())
     return h.hexdigest()[:16]
 
 
