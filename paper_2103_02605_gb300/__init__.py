@@ -137,6 +137,23 @@ def _u32_tensor(t, name):
     return t
 
 
+def _check_out(out, shape, dtypes, name="out"):
+    """A caller's output tensor: one of `dtypes`, contiguous, of exactly
+    `shape` (the library writes that many elements and no more)."""
+    if out.dtype not in dtypes:
+        raise TypeError(f"{name} must be one of {[str(d) for d in dtypes]}, got {out.dtype}")
+    if not out.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if tuple(out.shape) != tuple(shape):
+        raise ValueError(f"{name} must have shape {tuple(shape)}, got {tuple(out.shape)}")
+    return out
+
+
+def _dtypes(*names):
+    import torch
+    return tuple(getattr(torch, n) for n in names if hasattr(torch, n))
+
+
 # -- entry points --------------------------------------------------------------
 
 def fcirc_matvec(p: int, f: int, a, x, out=None, stream=None):
@@ -150,7 +167,7 @@ def fcirc_matvec(p: int, f: int, a, x, out=None, stream=None):
         raise ValueError("a and x must be 1-D of the same length")
     if out is None:
         out = torch.empty_like(a)
-    _u32_tensor(out, "out")
+    _check_out(out, a.shape, _dtypes("int32", "uint32"))
     st = _stream_handle(stream, a, x, out)
     _check(load().fcirc_matvec(p, f % p, a.data_ptr(), x.data_ptr(), out.data_ptr(), a.numel(), st),
            "fcirc_matvec")
@@ -168,7 +185,7 @@ def fcirc_matvec_t(p: int, f: int, a, x, out=None, stream=None):
         raise ValueError("a and x must be 1-D of the same length")
     if out is None:
         out = torch.empty_like(a)
-    _u32_tensor(out, "out")
+    _check_out(out, a.shape, _dtypes("int32", "uint32"))
     st = _stream_handle(stream, a, x, out)
     _check(load().fcirc_matvec_t(p, f % p, a.data_ptr(), x.data_ptr(), out.data_ptr(), a.numel(), st),
            "fcirc_matvec_t")
@@ -187,7 +204,7 @@ def fcirc_toeplitz_matvec(p: int, t, x, out=None, stream=None):
         raise ValueError("x must be 1-D of length n and t of length 2n - 1")
     if out is None:
         out = torch.empty_like(x)
-    _u32_tensor(out, "out")
+    _check_out(out, x.shape, _dtypes("int32", "uint32"))
     st = _stream_handle(stream, t, x, out)
     _check(load().fcirc_toeplitz_matvec(p, t.data_ptr(), x.data_ptr(), out.data_ptr(), n, st),
            "fcirc_toeplitz_matvec")
@@ -208,7 +225,7 @@ def fcirc_matvec_gf(a, x, f=(1, 0), out=None, stream=None):
     batch, n = a.shape[0], a.shape[1]
     if out is None:
         out = torch.empty_like(a)
-    _u32_tensor(out, "out")
+    _check_out(out, a.shape, _dtypes("int32", "uint32"))
     st = _stream_handle(stream, a, x, out)
     _check(load().fcirc_matvec_gf(a.data_ptr(), x.data_ptr(), out.data_ptr(), int(f[0]) % GF_P, int(f[1]) % GF_P,
                                   n, batch, st), "fcirc_matvec_gf")
@@ -231,6 +248,7 @@ def fcirc_matvec_ssa(a, x, K: int, f_exp: int = 0, out=None, stream=None):
         raise ValueError("a and x must have the same shape")
     if out is None:
         out = torch.empty_like(a)
+    _check_out(out, a.shape, _dtypes("int64", "uint64"))
     st = _stream_handle(stream, a, x, out)
     _check(load().fcirc_matvec_ssa(a.data_ptr(), x.data_ptr(), out.data_ptr(), K, f_exp, a.shape[1], a.shape[0], st),
            "fcirc_matvec_ssa")
@@ -279,7 +297,7 @@ class APlan:
             raise ValueError(f"x must be 1-D of length {self.n}")
         if out is None:
             out = torch.empty_like(x)
-        _u32_tensor(out, "out")
+        _check_out(out, x.shape, _dtypes("int32", "uint32"))
         st = _stream_handle(stream, x, out)
         _check(load().fcirc_matvec_aplan(self._h, x.data_ptr(), out.data_ptr(), st), "fcirc_matvec_aplan")
         return out
@@ -312,9 +330,12 @@ def poly_mul_int(P, Q, out=None, stream=None):
             raise TypeError(f"{nm} must be a 16-bit tensor, got {t.dtype}")
         if not t.is_contiguous() or t.dim() != 1:
             raise ValueError(f"{nm} must be 1-D contiguous")
+    if P.numel() == 0 or Q.numel() == 0:
+        raise ValueError("P and Q must not be empty")
     nout = P.numel() + Q.numel() - 1
     if out is None:
         out = torch.empty(nout, dtype=torch.int64, device=P.device)
+    _check_out(out, (nout,), _dtypes("int64", "uint64"))
     st = _stream_handle(stream, P, Q, out)
     _check(load().poly_mul_int(P.data_ptr(), P.numel(), Q.data_ptr(), Q.numel(), out.data_ptr(), st),
            "poly_mul_int")
@@ -331,8 +352,11 @@ def bigint_mul(A, B, out=None, stream=None):
             raise TypeError(f"{nm} must be a 16-bit tensor, got {t.dtype}")
         if not t.is_contiguous() or t.dim() != 1:
             raise ValueError(f"{nm} must be 1-D contiguous")
+    if A.numel() == 0 or B.numel() == 0:
+        raise ValueError("A and B must not be empty")
     if out is None:
         out = torch.empty(A.numel() + B.numel(), dtype=torch.int16, device=A.device)
+    _check_out(out, (A.numel() + B.numel(),), _dtypes("int16", "uint16"))
     st = _stream_handle(stream, A, B, out)
     _check(load().bigint_mul(A.data_ptr(), A.numel(), B.data_ptr(), B.numel(), out.data_ptr(), st),
            "bigint_mul")
@@ -347,9 +371,13 @@ def _batched_args(f, offsets, a, x, out):
             raise TypeError(f"{nm}: unexpected dtype {t.dtype}")
         if not t.is_contiguous() or t.dim() != 1:
             raise ValueError(f"{nm} must be 1-D contiguous")
+    if offsets.numel() != f.numel() + 1:
+        raise ValueError("offsets must hold one more entry than f (count + 1)")
+    if x.shape != a.shape:
+        raise ValueError("a and x must have the same length")
     if out is None:
         out = torch.empty_like(a)
-    return out
+    return _check_out(out, a.shape, _dtypes("int32", "uint32"))
 
 
 def fcirc_matvec_batched(p: int, f, offsets, a, x, out=None, stream=None):
@@ -381,6 +409,9 @@ class BatchedGraph:
     buffers (f, offsets, a, x, out); launch() replays it."""
 
     def __init__(self, p: int, f, offsets, a, x, out, total_n: int, stream=None):
+        _batched_args(f, offsets, a, x, out)
+        if total_n > a.numel():
+            raise ValueError("total_n exceeds the packed arrays")
         st = _stream_handle(stream, a, x, out)
         h = _vp()
         _check(load().fcirc_matvec_batched_graph(p, f.data_ptr(), offsets.data_ptr(), a.data_ptr(), x.data_ptr(),
@@ -425,6 +456,8 @@ def fcirc_matvec_c64(a, x, f=1.0, out=None, stream=None):
     if out is None:
         out = torch.empty_like(a)
     _c64(out, "out")
+    if out.shape != a.shape:
+        raise ValueError(f"out must have shape {tuple(a.shape)}")
     f = complex(f)
     st = _stream_handle(stream, a, x, out)
     _check(load().fcirc_matvec_c64(a.data_ptr(), x.data_ptr(), out.data_ptr(), f.real, f.imag, n, batch, st),
