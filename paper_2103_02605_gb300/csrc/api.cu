@@ -34,9 +34,9 @@ struct Arg {
     const void *user;   // caller pointer
     size_t bytes;
     bool in, out;
-    bool on_device;
-    bool pinned;        // page-locked host memory
-    void *d;            // device pointer used by the kernels
+    bool on_device = false;
+    bool pinned = false;        // page-locked host memory
+    void *d = nullptr;          // device pointer used by the kernels
 };
 
 int classify(Arg &a)
@@ -1047,17 +1047,25 @@ int fcirc_matvec_batched_graph(uint32_t p, const uint32_t *f, const uint64_t *of
             return fail(FCIRC_EINVAL, "fcirc_matvec_batched_graph: %p is not device memory", ptr);
         }
     }
-    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    (void)stream;   // the graph is captured on a private stream (below)
     BatchParams P{};
     FCIRC_TRY(batch_setup(p, count, total_n, P));
+    int dev = 0;
+    FCIRC_CUDA_TRY(cudaGetDevice(&dev));
     BatchGraph *g = new BatchGraph();
-    FCIRC_CUDA_TRY(cudaGetDevice(&g->dev));
+    g->dev = dev;
     const size_t bytes = batch_scratch_bytes(count, total_n);
     if (dev_alloc(&g->scratch, bytes) != cudaSuccess) {
         (void)cudaGetLastError();
         delete g;
         return fail(FCIRC_ENOMEM, "fcirc_matvec_batched_graph: cudaMalloc(%zu)", bytes);
     }
+    // every failure below releases the scratch and the handle
+    auto give_up = [&](int status) {
+        cudaFree(g->scratch);
+        delete g;
+        return status;
+    };
     P.f = f;
     P.offsets = offsets;
     P.a = a;
@@ -1067,8 +1075,17 @@ int fcirc_matvec_batched_graph(uint32_t p, const uint32_t *f, const uint64_t *of
     const int cfg = tuned_config(p, count, total_n);
     // capture on a private stream so that no other work lands in the graph
     cudaStream_t cs;
-    FCIRC_CUDA_TRY(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
-    FCIRC_CUDA_TRY(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+    cudaError_t e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+        (void)cudaGetLastError();
+        return give_up(fail(FCIRC_ECUDA, "cudaStreamCreateWithFlags: %s", cudaGetErrorString(e)));
+    }
+    e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) {
+        (void)cudaGetLastError();
+        cudaStreamDestroy(cs);
+        return give_up(fail(FCIRC_ECUDA, "cudaStreamBeginCapture: %s", cudaGetErrorString(e)));
+    }
     const int rc = launch_with_config(P, cfg, cs);
     cudaGraph_t graph = nullptr;
     const cudaError_t ce = cudaStreamEndCapture(cs, &graph);
@@ -1076,20 +1093,15 @@ int fcirc_matvec_batched_graph(uint32_t p, const uint32_t *f, const uint64_t *of
     if (rc != FCIRC_OK || ce != cudaSuccess) {
         (void)cudaGetLastError();
         if (graph) cudaGraphDestroy(graph);
-        cudaFree(g->scratch);
-        delete g;
-        return rc != FCIRC_OK ? rc : fail(FCIRC_ECUDA, "graph capture failed: %s", cudaGetErrorString(ce));
+        return give_up(rc != FCIRC_OK ? rc : fail(FCIRC_ECUDA, "graph capture failed: %s", cudaGetErrorString(ce)));
     }
     g->graph = graph;
     const cudaError_t ie = cudaGraphInstantiate(&g->exec, graph, 0);
     if (ie != cudaSuccess) {
         (void)cudaGetLastError();
         cudaGraphDestroy(graph);
-        cudaFree(g->scratch);
-        delete g;
-        return fail(FCIRC_ECUDA, "cudaGraphInstantiate: %s", cudaGetErrorString(ie));
+        return give_up(fail(FCIRC_ECUDA, "cudaGraphInstantiate: %s", cudaGetErrorString(ie)));
     }
-    (void)s;
     *out = reinterpret_cast<fcirc_graph_t>(g);
     return FCIRC_OK;
 }
