@@ -403,6 +403,21 @@ __global__ void __launch_bounds__(CShape<M>::CT) k_cbwd(const __grid_constant__ 
 // ---------------------------------------------------------------------------
 // host: twiddle tables per (f, n), FP64 -> FP32
 
+// Copies a plan's twiddle and inverse-twiddle tables to the device buffers
+// d and di; on failure frees both.
+int upload_tables(void *d, void *di, const void *h, const void *hi, size_t bytes)
+{
+    cudaError_t e = cudaMemcpy(d, h, bytes, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(di, hi, bytes, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        (void)cudaGetLastError();
+        cudaFree(d);
+        cudaFree(di);
+        return fail(FCIRC_ECUDA, "plan tables: cudaMemcpy: %s", cudaGetErrorString(e));
+    }
+    return FCIRC_OK;
+}
+
 struct CPlanKey {
     int dev;
     double re, im;
@@ -439,8 +454,7 @@ int get_ctables(double fre, double fim, uint64_t n, const float2 **tw, const flo
             cudaFree(d);
             return fail(FCIRC_ENOMEM, "complex plan: cudaMalloc failed");
         }
-        FCIRC_CUDA_TRY(cudaMemcpy(d, h.data(), n / 2 * sizeof(float2), cudaMemcpyHostToDevice));
-        FCIRC_CUDA_TRY(cudaMemcpy(di, hi.data(), n / 2 * sizeof(float2), cudaMemcpyHostToDevice));
+        FCIRC_TRY(upload_tables(d, di, h.data(), hi.data(), n / 2 * sizeof(float2)));
         it = g_cplans.emplace(key, std::make_pair(d, di)).first;
     }
     *tw = it->second.first;
@@ -490,8 +504,7 @@ int get_gtables(uint32_t fre, uint32_t fim, uint64_t n, const uint2 **tw, const 
             cudaFree(d);
             return fail(FCIRC_ENOMEM, "GF(p^2) plan: cudaMalloc failed");
         }
-        FCIRC_CUDA_TRY(cudaMemcpy(d, h.data(), n / 2 * sizeof(uint2), cudaMemcpyHostToDevice));
-        FCIRC_CUDA_TRY(cudaMemcpy(di, hi.data(), n / 2 * sizeof(uint2), cudaMemcpyHostToDevice));
+        FCIRC_TRY(upload_tables(d, di, h.data(), hi.data(), n / 2 * sizeof(uint2)));
         it = g_gplans.emplace(key, std::make_pair(d, di)).first;
     }
     *tw = it->second.first;
@@ -538,8 +551,7 @@ int get_stables(uint32_t K, uint32_t fe, uint64_t n, const int **tw, const int *
             cudaFree(d);
             return fail(FCIRC_ENOMEM, "Z/(2^K+1) plan: cudaMalloc failed");
         }
-        FCIRC_CUDA_TRY(cudaMemcpy(d, h.data(), n / 2 * sizeof(int), cudaMemcpyHostToDevice));
-        FCIRC_CUDA_TRY(cudaMemcpy(di, hi.data(), n / 2 * sizeof(int), cudaMemcpyHostToDevice));
+        FCIRC_TRY(upload_tables(d, di, h.data(), hi.data(), n / 2 * sizeof(int)));
         it = g_splans.emplace(key, std::make_pair(d, di)).first;
     }
     *tw = it->second.first;

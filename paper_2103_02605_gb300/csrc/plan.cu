@@ -176,7 +176,13 @@ static int upload(void **dptr, const void *src, size_t bytes)
         *dptr = nullptr;
         return fail(FCIRC_ENOMEM, "plan: cudaMalloc(%zu): %s", bytes, cudaGetErrorString(e));
     }
-    FCIRC_CUDA_TRY(cudaMemcpy(*dptr, src, bytes, cudaMemcpyHostToDevice));
+    e = cudaMemcpy(*dptr, src, bytes, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        (void)cudaGetLastError();
+        cudaFree(*dptr);
+        *dptr = nullptr;
+        return fail(FCIRC_ECUDA, "plan: cudaMemcpy(%zu): %s", bytes, cudaGetErrorString(e));
+    }
     return FCIRC_OK;
 }
 
