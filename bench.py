@@ -106,7 +106,8 @@ class ClockSampler:
     def __init__(self, index):
         self.index = index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+        import tempfile
+        self.path = os.path.join(tempfile.gettempdir(), f"fcirc_bench_clocks_{os.getpid()}.csv")
 
     def start(self):
         try:
@@ -218,9 +219,12 @@ def config_dict():
 # The kernels are bound by the SM's integer-multiply pipe (ncu:
 # sm__pipe_fmaheavy_cycles_active), not by HBM.  A 32-bit IMAD/IMUL occupies
 # that pipe for one slot per lane, a high-half or 64-bit-result multiply for
-# two; the pipe takes 16 lanes per SM sub-partition per cycle, so the peak is
-# 152 SMs x 4 x 16 slots x the SM clock.  Algorithmic slots per element, from
-# the arithmetic each kernel must do:
+# two; the pipe takes 16 lanes per SM sub-partition per cycle, so the nominal
+# peak is SMs x 4 x 16 slots x the SM clock.  The peak the headline divides
+# by is measured on the box instead (mul_peak_measured: the library's
+# multiply probe, independent low-half multiply chains, one slot each), with
+# the high-half rate beside it as a check of the two-slot count.
+# Algorithmic slots per element, from the arithmetic each kernel must do:
 #   Shoup product 4 (one high + two low), Montgomery reduction 3, 64-bit
 #   product 2, twiddle generation 8, Garner CRT 21.
 # Per circulant element N = 2^24 of the polynomial product (3 primes):
@@ -231,7 +235,28 @@ MUL_SLOTS_PER_ELEM = {"k_colfwd": 138, "k_tile4096": 249, "k_colinv": 93}
 MUL_SLOTS_PER_ELEM["k_colfwd4"] = MUL_SLOTS_PER_ELEM["k_colfwd"]    # same pass, four columns per thread
 MUL_SLOTS_PER_ELEM["k_colinv4x3"] = MUL_SLOTS_PER_ELEM["k_colinv"]
 SLOTS_PER_SM_CYCLE = 4 * 16
-N_SMS = 152
+
+
+def sm_count():
+    """Multiprocessors of the current device (152 on a GB300)."""
+    import torch
+    return int(torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count)
+
+
+_MUL_PEAK = {}
+
+
+def mul_peak_measured(F):
+    """Measured multiply-pipe peak of the current device in T slots/s: the
+    fastest of the library's probe configurations with low-half multiplies
+    (one slot each); the high-half rate (two slots each under the model) is
+    reported beside it.  Measured once per process."""
+    if "v" not in _MUL_PEAK:
+        lo = max(F.prof_mul_probe(0, c, 4096)[1] for c in (2, 4, 8))
+        hi = max(F.prof_mul_probe(1, c, 4096)[1] for c in (2, 4, 8))
+        _MUL_PEAK["v"] = {"tslots": lo / 1e12, "lo_mul_per_s": lo, "hi_mul_per_s": hi,
+                          "hi_slots_per_mul": lo / hi}
+    return _MUL_PEAK["v"]
 
 
 def kernel_bytes():
@@ -313,7 +338,8 @@ def _time(fn, reps, flush, stream, warm=2):
     return statistics.median(ts), min(ts)
 
 
-def _extra_roofline(ms, elems, slots_per_elem=None, bytes_per_elem=None, flops_per_elem=None, bound=None):
+def _extra_roofline(ms, elems, slots_per_elem=None, bytes_per_elem=None, flops_per_elem=None, bound=None,
+                    mul_peak_slots=None, n_sms=None):
     """Roofline fractions of one secondary workload from its median time:
     algorithmic multiply slots (the headline's unit: a Shoup product is 4,
     so a butterfly is 2 per element and level), compulsory HBM bytes and
@@ -322,17 +348,19 @@ def _extra_roofline(ms, elems, slots_per_elem=None, bytes_per_elem=None, flops_p
     slots per cycle; FP32: 152 SMs x 128 lanes x 2 flops per cycle)."""
     peaks, kind = measured_peaks()
     mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    n_sms = sm_count() if n_sms is None else n_sms
     sec = ms * 1e-3
     r = {"peak_source": kind}
     if bound:
         r["bound"] = bound
     if slots_per_elem is not None:
         ach = slots_per_elem * elems / sec / 1e12
-        pk = N_SMS * SLOTS_PER_SM_CYCLE * mhz * 1e6 / 1e12
-        r["mul_slots"] = {"per_elem": slots_per_elem, "achieved_tslots": ach, "peak_tslots": pk, "frac": ach / pk}
+        pk = mul_peak_slots if mul_peak_slots else n_sms * SLOTS_PER_SM_CYCLE * mhz * 1e6 / 1e12
+        r["mul_slots"] = {"per_elem": slots_per_elem, "achieved_tslots": ach, "peak_tslots": pk, "frac": ach / pk,
+                          "peak": "measured (multiply probe)" if mul_peak_slots else "nominal"}
     if flops_per_elem is not None:
         ach = flops_per_elem * elems / sec / 1e12
-        pk = N_SMS * 128 * 2 * mhz * 1e6 / 1e12
+        pk = n_sms * 128 * 2 * mhz * 1e6 / 1e12
         r["fp32"] = {"per_elem": flops_per_elem, "achieved_tflops": ach, "peak_tflops": pk, "frac": ach / pk}
     if bytes_per_elem is not None:
         ach = bytes_per_elem * elems / sec / 1e9
@@ -467,31 +495,35 @@ def run_extras(F, I, dev, stream):
     #  * large integers, 2^26 x 2^26 bits (circulant N = 2^23, 3 primes):
     #    3 primes x 3 trees x 22 levels x 2 slots + 21 for the CRT per
     #    circulant element; 2 bytes in per input limb, 2 out per product limb.
+    import functools
+    R = functools.partial(_extra_roofline, mul_peak_slots=mul_peak_measured(F)["tslots"])
     n24 = 1 << 24
-    out["fcirc_matvec_n2^24"]["roofline"] = _extra_roofline(out["fcirc_matvec_n2^24"]["ms"], n24, 138, 12)
-    out["fcirc_matvec_t_n2^24"]["roofline"] = _extra_roofline(out["fcirc_matvec_t_n2^24"]["ms"], n24, 142, 12)
-    out["fcirc_matvec_aplan_n2^24"]["roofline"] = _extra_roofline(out["fcirc_matvec_aplan_n2^24"]["ms"], n24, 92, 12)
+    out["fcirc_matvec_n2^24"]["roofline"] = R(out["fcirc_matvec_n2^24"]["ms"], n24, 138, 12)
+    out["fcirc_matvec_t_n2^24"]["roofline"] = R(out["fcirc_matvec_t_n2^24"]["ms"], n24, 142, 12)
+    out["fcirc_matvec_aplan_n2^24"]["roofline"] = R(out["fcirc_matvec_aplan_n2^24"]["ms"], n24, 92, 12)
     tot = float(np.sum(nn.astype(np.float64)))
     bslots = float(np.sum(nn.astype(np.float64) * 6 * (np.log2(nn.astype(np.float64)) - 1))) / tot
-    out["batched_10000_uneven"]["roofline"] = _extra_roofline(out["batched_10000_uneven"]["graph_ms"], tot,
+    out["batched_10000_uneven"]["roofline"] = R(out["batched_10000_uneven"]["graph_ms"], tot,
                                                               bslots, 12)
-    out["complex_fwd_bwd_4096x1024"]["roofline"] = _extra_roofline(out["complex_fwd_bwd_4096x1024"]["fused_ms"],
+    out["complex_fwd_bwd_4096x1024"]["roofline"] = R(out["complex_fwd_bwd_4096x1024"]["fused_ms"],
                                                                    4096 * 1024, None, 64, 3 * (3 * 9 * 5 + 17),
                                                                    bound="shared-memory bandwidth (ncu)")
-    out["gfp2_10000x2048"]["roofline"] = _extra_roofline(out["gfp2_10000x2048"]["ms"], 10000 * 2048, None, 24,
+    out["gfp2_10000x2048"]["roofline"] = R(out["gfp2_10000x2048"]["ms"], 10000 * 2048, None, 24,
                                                          bound="alu (ncu)")
-    out["ssa_K128_20000x256"]["roofline"] = _extra_roofline(out["ssa_K128_20000x256"]["ms"], 20000 * 256, None, 72,
+    out["ssa_K128_20000x256"]["roofline"] = R(out["ssa_K128_20000x256"]["ms"], 20000 * 256, None, 72,
                                                             bound="alu (ncu)")
-    out["bigint_2^26bit"]["roofline"] = _extra_roofline(out["bigint_2^26bit"]["ms"], 1 << 23,
+    out["bigint_2^26bit"]["roofline"] = R(out["bigint_2^26bit"]["ms"], 1 << 23,
                                                         3 * 3 * 22 * 2 + 21, (A.size + B.size) * 4 / (1 << 23))
     return out
 
 
 # Kernels that only the secondary workloads launch (by the prefix of the
-# library's trace names, which the CUDA function names share), profiled by
-#   ncu --set full --clock-control none -k regex:"<PROFILE_EXTRA_KERNELS>"
-#       -s SKIP -c COUNT python bench.py --profile-extras
-# with SKIP and COUNT as --profile-extras prints them.
+# library's trace names, which the CUDA function names share).  Each is
+# profiled on its own, one launch per capture:
+#   ncu --set full --clock-control none -k regex:<K> -s SKIP_K -c 1
+#       python bench.py --profile-extras
+# with SKIP_K as --profile-extras prints it for kernel K (its launches before
+# the second round).
 PROFILE_EXTRA_KERNELS = "k_tile4096|k_cfwd|k_cbwd|k_bmain|k_gfwd|k_sfwd"
 
 
@@ -502,7 +534,8 @@ def profile_extras(F, I, dev, stream):
     10,000 uneven batched instances in one graph launch, GF(p^2) 10,000 x
     2048 and Z/(2^128 + 1) 20,000 x 256.  Prints ncu's skip (the launches
     of PROFILE_EXTRA_KERNELS before the second round) and count (one
-    round's)."""
+    round's), and for each kernel K of PROFILE_EXTRA_KERNELS the skip that
+    puts a one-launch capture of K on its second-round launch."""
     import re
     import numpy as np
     import torch
@@ -519,7 +552,8 @@ def profile_extras(F, I, dev, stream):
     plan = F.APlan(I.P1, 1, da, stream=stream)   # its row-vector tile runs here
     torch.cuda.synchronize()
     F.prof_stop()
-    setup = matches(F.prof_report())
+    setup_rep = F.prof_report()
+    setup = matches(setup_rep)
     ca, cx, cg = (torch.from_numpy(v).to(dev) for v in I.complex_layer(4096, 1024))
     nn, f, off, ba, bx = I.batched_mod()
     bf = torch.from_numpy(f.view(np.int32)).to(dev)
@@ -555,7 +589,59 @@ def profile_extras(F, I, dev, stream):
     graph.destroy()
     plan.destroy()
     print(f"PROFILE_EXTRA_SKIP={setup + per_round} PROFILE_EXTRA_COUNT={per_round}", flush=True)
+    for k in PROFILE_EXTRA_KERNELS.split("|"):
+        kp = re.compile(k)
+        n0 = sum(c for name, (c, _) in setup_rep.items() if kp.match(name))
+        n1 = 1 if k == "k_bmain" else sum(c for name, (c, _) in rep.items() if kp.match(name))
+        print(f"PROFILE_EXTRA {k} SKIP={n0 + n1}", flush=True)
     return 0
+
+
+def run_batched_shard(F, I, dev, stream, ws, rank):
+    """The uneven batch (10,000 instances, sizes 2^6..2^16) split over the
+    ranks with fcirc_batched_partition: each rank packs its instances, runs
+    them in one graph launch, and keeps its results -- no collective on the
+    data path.  Whole-batch time = the slowest rank's (barrier + max over
+    ranks around ten timed launches)."""
+    import numpy as np
+    import torch
+    nn, f, off, a, x = I.batched_mod()
+    members, loads = F.batched_partition(off, ws, rank)
+    loc, fs, as_, xs = F.batched_shard(members, off, f, a, x)
+    df = torch.from_numpy(fs.view(np.int32)).to(dev)
+    doff = torch.from_numpy(loc.view(np.int64)).to(dev)
+    da = torch.from_numpy(as_.view(np.int32)).to(dev)
+    dx = torch.from_numpy(xs.view(np.int32)).to(dev)
+    dc = torch.empty_like(da)
+    graph = F.BatchedGraph(I.P1, df, doff, da, dx, dc, int(loc[-1]), stream=stream)
+    for _ in range(3):
+        graph.launch(stream=stream)
+    torch.cuda.synchronize()
+    # this rank's smallest and largest instances against the oracle
+    from oracle import oracle
+    got = dc.cpu().numpy().view(np.uint32)
+    sizes = loc[1:] - loc[:-1]
+    for j in {int(np.argmin(sizes)), int(np.argmax(sizes))}:
+        i, s0, s1 = int(members[j]), int(loc[j]), int(loc[j + 1])
+        rows = np.unique(np.r_[0, s1 - s0 - 1, np.arange(0, s1 - s0, 997)]).astype(np.uint64)
+        want = oracle.fcirc_matvec_mod_rows(I.P1, int(f[i]), a[int(off[i]):int(off[i + 1])],
+                                            x[int(off[i]):int(off[i + 1])], rows)
+        assert np.array_equal(got[s0 + rows.astype(np.int64)], want), f"shard instance {i} differs"
+    barrier(ws)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(10):
+        graph.launch(stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = max_over_ranks(e0.elapsed_time(e1) / 10, ws)
+    barrier(ws)
+    graph.destroy()
+    total = int(off[-1])
+    return {"ranks": ws, "instances_rank0": int(members.size), "ms": ms, "Gelem_s": total / (ms * 1e-3) / 1e9,
+            "load_imbalance": float(max(loads) / (sum(loads) / len(loads))),
+            "split": "fcirc_batched_partition (LPT on n log2 n), no collective on the data path"}
 
 
 def run_ours(args, ws, rank, local):
@@ -647,19 +733,43 @@ def run_ours(args, ws, rank, local):
         ser.append(time.perf_counter() - ta)
     assert torch.equal(sets[0][2], want), "e2e output mismatch (serial)"
     barrier(ws)
+    # per step: CUDA events on its stream around the call (its H2D copies,
+    # kernels and D2H copy) against one origin event, and the host time the
+    # call itself takes (a call that waits for its stream takes a step's
+    # whole device time on the host and leaves nothing to overlap)
+    origin = torch.cuda.Event(enable_timing=True)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(n_e2e)]
+    host_call = []
+    origin.record(streams[0])
     ta = time.perf_counter()
     for k in range(n_e2e):
         Ph, Qh, Oh = sets[k % NSTREAMS]
-        streams[k % NSTREAMS].synchronize()   # the step that last used this buffer set is done
-        F.poly_mul_int(Ph, Qh, out=Oh, stream=streams[k % NSTREAMS])
+        st_ = streams[k % NSTREAMS]
+        st_.synchronize()   # the step that last used this buffer set is done
+        if k == 0:
+            st_.wait_event(origin)
+        ev[k][0].record(st_)
+        tc = time.perf_counter()
+        F.poly_mul_int(Ph, Qh, out=Oh, stream=st_)
+        host_call.append(time.perf_counter() - tc)
+        ev[k][1].record(st_)
     for st_ in streams:
         st_.synchronize()
     e2e_s = max_over_ranks((time.perf_counter() - ta) / n_e2e, ws)
     e2e_serial_s = max_over_ranks(statistics.mean(ser), ws)
+    spans = [(origin.elapsed_time(a), origin.elapsed_time(b)) for a, b in ev]
+    busy = sum(b - a for a, b in spans)
+    wall = max(b for _, b in spans) - min(a for a, _ in spans)
+    e2e_diag = {"host_ms_per_call_median": 1e3 * statistics.median(host_call),
+                "device_ms_per_step_median": statistics.median(b - a for a, b in spans),
+                "overlap": busy / wall if wall > 0 else None,
+                "note": "overlap = sum of per-step device spans / their union's extent (1: none)"}
     for Ph, Qh, Oh in sets:
         assert torch.equal(Oh, want), "e2e output mismatch (pipelined)"
     if sampler:
         sampler.stop()
+    # with several ranks, the uneven batch split over them (every rank runs)
+    shard = run_batched_shard(F, I, dev, stream, ws, rank) if ws > 1 else None
 
     if rank != 0:
         return 0
@@ -670,7 +780,10 @@ def run_ours(args, ws, rank, local):
     dname, (dcnt, dms) = dom
     avg_s = dms / dcnt * 1e-3
     sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
-    mul_peak = N_SMS * SLOTS_PER_SM_CYCLE * sm_mhz * 1e6 / 1e12          # T slots/s
+    n_sms = sm_count()
+    mul_nominal = n_sms * SLOTS_PER_SM_CYCLE * sm_mhz * 1e6 / 1e12      # T slots/s
+    mp = mul_peak_measured(F)
+    mul_peak = mp["tslots"]
     mul_achieved = MUL_SLOTS_PER_ELEM.get(dname, 0) * NCIRC / avg_s / 1e12
     hbm_achieved = kb.get(dname, 0) / avg_s / 1e9
     rate, m, dt, cores = oracle_rate(Pn, Qn, 10.0)
@@ -684,7 +797,12 @@ def run_ours(args, ws, rank, local):
         "roofline": {"bound": "alu", "kernel": dname, "achieved": mul_achieved,
                      "peak": mul_peak, "unit": "T int-mul slots/s",
                      "frac": mul_achieved / mul_peak, "traffic": ncu_traffic(dname),
-                     "peak_source": f"152 SMs x 64 multiply slots/cycle x sm_max_mhz ({peak_kind} MEASURED_PEAKS clock)",
+                     "peak_source": "measured: the library's multiply probe (16 independent low-half "
+                                    "multiply chains per thread, one slot each), on this device in this run",
+                     "peak_probe": {"lo_mul_per_s": mp["lo_mul_per_s"], "hi_mul_per_s": mp["hi_mul_per_s"],
+                                    "hi_slots_per_mul": mp["hi_slots_per_mul"],
+                                    "nominal_tslots": mul_nominal, "n_sms": n_sms, "nominal_mhz": sm_mhz,
+                                    "frac_of_nominal": mul_achieved / mul_nominal},
                      "algorithmic_slots_per_launch": MUL_SLOTS_PER_ELEM.get(dname, 0) * NCIRC,
                      "hbm": {"achieved_gbs": hbm_achieved, "peak_gbs": float(peaks["hbm_gbs"]),
                              "frac": hbm_achieved / float(peaks["hbm_gbs"]),
@@ -698,13 +816,16 @@ def run_ours(args, ws, rank, local):
                         "(a step's copies overlap its neighbours' kernels)",
                 "ms_per_step": 1e3 * e2e_s,
                 "serial_value": ws * UNITS / e2e_serial_s / 1e9,
-                "serial_ms_per_step": 1e3 * e2e_serial_s},
+                "serial_ms_per_step": 1e3 * e2e_serial_s,
+                "pipeline": e2e_diag},
         "clocks": clocks,
         "gpu_launches": int(launches),
         "kernels": {k: {"launches": c, "avg_us": 1e3 * t / c, "share": t / sum(v[1] for v in prof.values())}
                     for k, (c, t) in sorted(prof.items())},
         "extra": extras,
     }
+    if shard:
+        line["batched_sharded"] = shard
     print(json.dumps(line), flush=True)
     return 0
 

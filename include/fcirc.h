@@ -141,6 +141,12 @@ int fcirc_matvec_t(uint32_t p, uint32_t f, const uint32_t *a, const uint32_t *x,
  * device also looks up the array's device address (once per device, with
  * that device current); make that first call before capturing any stream
  * into a CUDA graph.
+ *
+ * Which tables the array holds is remembered on the host, so a call made
+ * while `stream` is being captured into a graph returns FCIRC_EINVAL and
+ * enqueues nothing.  Unlike the other entry points it runs no input range
+ * check under fcirc_set_checks(1): that check reports through a status word
+ * the library would have to allocate.  Inputs must be < p.
  */
 int fcirc_matvec_noalloc(uint32_t p, uint32_t f, const uint32_t *a, const uint32_t *x,
                          uint32_t *c, uint64_t n, void *stream);
@@ -236,6 +242,33 @@ int fcirc_matvec_batched_graph(uint32_t p, const uint32_t *f, const uint64_t *of
                                fcirc_graph_t *graph);
 int fcirc_graph_launch(fcirc_graph_t graph, void *stream);
 int fcirc_graph_destroy(fcirc_graph_t graph);
+
+/*
+ * fcirc_batched_partition -- splits a batch over `nranks` processes (one
+ * GPU each) for fcirc_matvec_batched.  The instances of a batch are
+ * independent products, just as the two halves of one product are after a
+ * halving step (the structure argument in the proof of Theorem 1), so a
+ * batch shards with no exchange between ranks: each rank runs its own
+ * instances and keeps their results.
+ *
+ * Host-only (no GPU call), deterministic: every rank computes the same
+ * partition from the same offsets, so no rank has to send it.  Longest
+ * processing time first: instances sorted by the cost n_i * max(log2 n_i, 1)
+ * of Algorithm 1 (largest first, ties by index), each given to the rank
+ * with the least cost so far (ties to the lowest rank).
+ *
+ *   offsets   HOST uint64[count + 1], as for fcirc_matvec_batched
+ *             (non-decreasing; sizes need not be powers of two here).
+ *   nranks    1 .. 65536; rank < nranks.
+ *   members   caller's uint32[count]: receives the indices of the
+ *             instances of `rank`, ascending, in members[0 .. *nmembers).
+ *   loads     NULL, or the caller's double[nranks]: every rank's total cost.
+ *
+ * Returns FCIRC_OK, or FCIRC_EINVAL (null pointer, decreasing offsets, bad
+ * nranks or rank), or FCIRC_ENOMEM (host memory).
+ */
+int fcirc_batched_partition(const uint64_t *offsets, uint32_t count, uint32_t nranks, uint32_t rank,
+                            uint32_t *members, uint32_t *nmembers, double *loads);
 
 /*
  * poly_mul_int -- exact product of two polynomials with 16-bit unsigned

@@ -34,6 +34,21 @@ int fcirc_prof_report(char *buf, uint64_t len);
 /* Number of kernel launches recorded since fcirc_prof_start(). */
 uint64_t fcirc_prof_launches(void);
 
+/*
+ * Measures the SM's integer-multiply throughput, the unit that bounds the
+ * modular kernels (each butterfly is one Shoup product: a high-half and two
+ * low-half 32-bit multiplies).  Launches ctas_per_sm (1..8) CTAs of 256
+ * threads per SM of the current device; every thread runs 16 independent
+ * chains of `iters` multiplies of one kind (kind 0: low-half v * a + b;
+ * kind 1: high-half hi(v * a) + b), so the multiply pipe and not latency sets
+ * the rate.  Times five launches with CUDA events on a stream of its own
+ * (synchronising) and writes the fastest launch's time in *ms and its rate
+ * in multiplies per second in *mul_per_s.  Allocates and frees a 1 KiB
+ * sink.  Returns FCIRC_OK, FCIRC_EINVAL (bad arguments), FCIRC_ENOMEM or
+ * FCIRC_ECUDA.
+ */
+int fcirc_prof_mul_probe(int kind, uint32_t ctas_per_sm, uint32_t iters, double *ms, double *mul_per_s);
+
 #ifdef __cplusplus
 }
 #endif

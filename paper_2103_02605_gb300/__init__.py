@@ -28,9 +28,10 @@ __all__ = [
     "FcircError", "library_path", "load",
     "fcirc_matvec", "fcirc_matvec_t", "fcirc_toeplitz_matvec", "fcirc_matvec_gf", "GF_P", "fcirc_matvec_ssa", "fcirc_matvec_noalloc", "APlan", "poly_mul_int", "bigint_mul",
     "fcirc_matvec_c64", "fcirc_matvec_backward", "fcirc_layer",
-    "fcirc_matvec_batched", "batched_autotune", "BatchedGraph", "sync_status", "release", "set_checks",
+    "fcirc_matvec_batched", "batched_autotune", "BatchedGraph", "batched_partition", "batched_shard",
+    "sync_status", "release", "set_checks",
     "nth_root", "node_twiddle", "leaf_param", "twiddle_from_factor",
-    "prof_start", "prof_stop", "prof_report", "prof_launches",
+    "prof_start", "prof_stop", "prof_report", "prof_launches", "prof_mul_probe",
     "PRIMES",
 ]
 
@@ -62,6 +63,7 @@ _SIGNATURES = {
     "fcirc_matvec_batched_graph": ([_u32, _vp, _vp, _vp, _vp, _vp, _u32, _u64, _vp, ctypes.POINTER(_vp)], _i32),
     "fcirc_graph_launch": ([_vp, _vp], _i32),
     "fcirc_graph_destroy": ([_vp], _i32),
+    "fcirc_batched_partition": ([_vp, _u32, _u32, _u32, _vp, ctypes.POINTER(_u32), _vp], _i32),
     "fcirc_matvec_backward": ([_vp, _vp, _vp, ctypes.c_double, ctypes.c_double, _vp, _vp, _u64, _u64, _vp],
                               _i32),
     "fcirc_sync_status": ([_vp], _i32),
@@ -79,6 +81,8 @@ _SIGNATURES = {
     "fcirc_prof_stop": ([], _i32),
     "fcirc_prof_report": ([ctypes.c_char_p, _u64], _i32),
     "fcirc_prof_launches": ([], _u64),
+    "fcirc_prof_mul_probe": ([ctypes.c_int, _u32, _u32, ctypes.POINTER(ctypes.c_double),
+                              ctypes.POINTER(ctypes.c_double)], _i32),
 }
 
 
@@ -404,6 +408,56 @@ def batched_autotune(p: int, f, offsets, a, x, out=None, stream=None):
     return ch.value, cps.value, tl.value
 
 
+def batched_partition(offsets, nranks: int, rank: int):
+    """The instances of `rank` when a batch is split over `nranks` ranks
+    (include/fcirc.h, fcirc_batched_partition: longest processing time first
+    on n log2 n, the same on every rank).  offsets: host uint64/int64
+    sequence of count + 1 offsets.  Returns (members, loads): the ascending
+    instance indices of `rank` (numpy uint32) and every rank's total cost
+    (numpy float64).  Host only."""
+    import numpy as np
+    off = np.ascontiguousarray(np.asarray(offsets).astype(np.uint64, copy=False))
+    if off.ndim != 1 or off.size < 1:
+        raise ValueError("offsets must be a 1-D sequence of count + 1 entries")
+    count = off.size - 1
+    members = np.empty(max(count, 1), dtype=np.uint32)
+    loads = np.empty(max(int(nranks), 1), dtype=np.float64)
+    nm = _u32()
+    _check(load().fcirc_batched_partition(off.ctypes.data, count, int(nranks), int(rank), members.ctypes.data,
+                                          ctypes.byref(nm), loads.ctypes.data), "fcirc_batched_partition")
+    return members[:nm.value].copy(), loads[:int(nranks)].copy()
+
+
+def batched_shard(members, offsets, *arrays):
+    """Packs the instances `members` of a batch back to back: returns the
+    shard's offsets (uint64, len(members) + 1) and, for each packed array
+    (instance i on [offsets[i], offsets[i+1])) or per-instance array (one
+    entry per instance) given, the shard's copy.  Host (numpy) arrays."""
+    import numpy as np
+    off = np.asarray(offsets).astype(np.uint64, copy=False)
+    members = np.asarray(members, dtype=np.int64)
+    count = off.size - 1
+    sizes = (off[1:] - off[:-1])[members]
+    loc = np.zeros(members.size + 1, dtype=np.uint64)
+    np.cumsum(sizes, out=loc[1:])
+    total = int(off[-1])
+    idx = None
+    out = [loc]
+    for arr in arrays:
+        arr = np.asarray(arr)
+        if arr.shape[0] == count and count != total:
+            out.append(arr[members].copy())
+            continue
+        if arr.shape[0] != total:
+            raise ValueError("an array is neither packed (offsets[-1] entries) nor per instance (count entries)")
+        if idx is None:
+            starts = off[:-1][members].astype(np.int64)
+            idx = (np.repeat(starts - loc[:-1].astype(np.int64), sizes.astype(np.int64))
+                   + np.arange(int(loc[-1]), dtype=np.int64))
+        out.append(arr[idx].copy())
+    return tuple(out)
+
+
 class BatchedGraph:
     """The batched launch sequence captured into a CUDA graph for fixed device
     buffers (f, offsets, a, x, out); launch() replays it."""
@@ -555,6 +609,16 @@ def prof_report() -> dict:
 
 def prof_launches() -> int:
     return int(load().fcirc_prof_launches())
+
+
+def prof_mul_probe(kind: int, ctas_per_sm: int = 4, iters: int = 4096):
+    """(ms, multiplies per second) of the library's integer-multiply probe
+    on the current device: kind 0 low-half, kind 1 high-half 32-bit
+    multiplies (include/fcirc_prof.h)."""
+    ms, rate = ctypes.c_double(), ctypes.c_double()
+    _check(load().fcirc_prof_mul_probe(int(kind), int(ctas_per_sm), int(iters), ctypes.byref(ms),
+                                       ctypes.byref(rate)), "fcirc_prof_mul_probe")
+    return ms.value, rate.value
 
 
 # -- host-side plan numbers (no GPU needed) -------------------------------------

@@ -250,13 +250,21 @@ extern "C" int fcirc_matvec_noalloc(uint32_t p, uint32_t f, const uint32_t *a, c
     int dev = 0;
     FCIRC_CUDA_TRY(cudaGetDevice(&dev));
     if (dev < 0 || dev >= 64) return fail(FCIRC_EINVAL, "fcirc_matvec_noalloc: device %d out of range", dev);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    // The table cache below is host state: a call recorded into a graph could
+    // not know which tables the array holds when the graph is replayed, and
+    // a table upload recorded from a host vector freed on return would copy
+    // garbage.  So a call on a stream that is being captured does nothing.
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    FCIRC_CUDA_TRY(cudaStreamIsCapturing(s, &cap));
+    if (cap != cudaStreamCaptureStatusNone)
+        return fail(FCIRC_EINVAL, "fcirc_matvec_noalloc: the stream is being captured into a graph");
+
     for (const void *ptr : {(const void *)a, (const void *)x, (const void *)c}) {
         bool ok;
         FCIRC_TRY(is_device_ptr(ptr, dev, ok));
         if (!ok) return fail(FCIRC_EINVAL, "fcirc_matvec_noalloc: %p is not device memory of device %d", ptr, dev);
     }
-    cudaStream_t s = static_cast<cudaStream_t>(stream);
-
     std::lock_guard<std::mutex> lk(g_mu);
     DevState &ds = g_dev[dev];
     if (!ds.ready) {

@@ -132,8 +132,19 @@ int device_status_word(uint32_t **out)
     std::lock_guard<std::mutex> lk(g_scratch_mu);
     uint32_t *&w = g_status[dev];
     if (!w) {
-        FCIRC_CUDA_TRY(cudaMalloc(&w, 256));
-        FCIRC_CUDA_TRY(cudaMemset(w, 0, 256));
+        // through dev_alloc, so that the allocation fault injection reaches it
+        void *ptr = nullptr;
+        const cudaError_t e = dev_alloc(&ptr, 256);
+        if (e != cudaSuccess) {
+            (void)cudaGetLastError();
+            return fail(FCIRC_ENOMEM, "status word: cudaMalloc(256) failed: %s", cudaGetErrorString(e));
+        }
+        const cudaError_t z = cudaMemset(ptr, 0, 256);
+        if (z != cudaSuccess) {
+            (void)cudaFree(ptr);
+            return fail(FCIRC_ECUDA, "status word: cudaMemset failed: %s", cudaGetErrorString(z));
+        }
+        w = static_cast<uint32_t *>(ptr);
     }
     *out = w;
     return FCIRC_OK;

@@ -29,7 +29,8 @@ def test_digest_ignores_a_comment_edit_and_sees_a_code_edit(tmp_path, monkeypatc
 
 
 def test_extra_roofline_arithmetic():
-    r = bench._extra_roofline(1.0, 1 << 20, slots_per_elem=100, bytes_per_elem=12, flops_per_elem=50, bound="x")
+    r = bench._extra_roofline(1.0, 1 << 20, slots_per_elem=100, bytes_per_elem=12, flops_per_elem=50, bound="x",
+                              n_sms=152)
     peaks, _ = bench.measured_peaks()
     mhz = float(peaks.get("sm_max_mhz", 2070.0))
     assert r["bound"] == "x"
@@ -38,3 +39,9 @@ def test_extra_roofline_arithmetic():
     assert r["fp32"]["peak_tflops"] == pytest.approx(152 * 256 * mhz * 1e6 / 1e12)
     assert r["hbm"]["achieved_gbs"] == pytest.approx(12 * (1 << 20) / 1e-3 / 1e9)
     assert r["hbm"]["frac"] == pytest.approx(r["hbm"]["achieved_gbs"] / float(peaks["hbm_gbs"]))
+
+    # with a measured multiply peak the fraction divides by it
+    m = bench._extra_roofline(1.0, 1 << 20, slots_per_elem=100, mul_peak_slots=10.0, n_sms=152)
+    assert m["mul_slots"]["peak_tslots"] == 10.0
+    assert m["mul_slots"]["frac"] == pytest.approx(100 * (1 << 20) / 1e-3 / 1e12 / 10.0)
+    assert m["mul_slots"]["peak"].startswith("measured")

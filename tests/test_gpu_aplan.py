@@ -53,6 +53,12 @@ def test_plan_equals_plain_product(F, orc, m):
             assert np.array_equal(got, want), (m, k)
             if n <= 1 << 12:
                 assert np.array_equal(got, orc.fcirc_matvec_mod(p, f, a, x))
+            else:
+                # the plan's tile variants against the oracle too, on rows
+                # spread over every tile and both ends
+                rows = np.unique(np.r_[0, 1, 4095, 4096, n // 2, n - 2, n - 1,
+                                       np.random.default_rng(m + 10 * k).integers(0, n, 96)]).astype(np.uint64)
+                assert np.array_equal(got[rows.astype(np.int64)], orc.fcirc_matvec_mod_rows(p, f, a, x, rows)), (m, k)
 
 
 def test_plan_on_two_streams_and_host_buffers(F, orc):

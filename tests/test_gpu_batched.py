@@ -153,3 +153,24 @@ def test_host_buffers(F, orc):
     c = F.fcirc_matvec_batched(P1, torch.from_numpy(f.view(np.int32)), torch.from_numpy(off.view(np.int64)),
                                torch.from_numpy(a.view(np.int32)), torch.from_numpy(x.view(np.int32)))
     check(orc, P1, f, off, a, x, c.numpy().view(np.uint32))
+
+
+@pytest.mark.parametrize("ws", [2, 3])
+def test_sharded_batch_equals_the_whole(F, orc, ws):
+    """The batch split with fcirc_batched_partition, each shard packed and run
+    on its own (the ranks of a multi-GPU job, here one after the other on
+    one GPU): every instance's result equals the unsplit launch's, and the
+    oracle's."""
+    sizes = [1 << e for e in np.random.default_rng(ws).integers(0, 15, 150)]
+    f, off, a, x = make_batch(sizes, seed=40 + ws)
+    whole = run(F, f, off, a, x)
+    check(orc, P1, f, off, a, x, whole, seed=ws)
+    seen = np.zeros(len(sizes), bool)
+    for r in range(ws):
+        members, loads = F.batched_partition(off, ws, r)
+        loc, fs, as_, xs = F.batched_shard(members, off, f, a, x)
+        part = run(F, fs, loc, as_, xs)
+        for j, i in enumerate(members):
+            assert np.array_equal(part[int(loc[j]):int(loc[j + 1])], whole[int(off[i]):int(off[i + 1])]), (r, i)
+        seen[members] = True
+    assert seen.all()

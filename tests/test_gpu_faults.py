@@ -112,3 +112,24 @@ def test_fixed_matrix_plan_allocation_failure(F, orc):
         assert np.array_equal(c.cpu().numpy().view(np.uint32)[:64], orc.fcirc_matvec_mod_rows(
             P1, 1, a, x, np.arange(64, dtype=np.uint64)))
     assert F.sync_status() == 0
+
+
+def test_status_word_allocation_failure():
+    """The device status word is allocated through the same function as every
+    other device buffer, so an injected failure reaches it too.  It is kept
+    for the life of the process, hence a fresh process: its first use fails
+    with FCIRC_ENOMEM, and the next succeeds."""
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    code = (
+        "import paper_2103_02605_gb300 as F\n"
+        "L = F.load()\n"
+        "L.fcirc_debug_fail_alloc(0)\n"
+        "rc = L.fcirc_sync_status(None)\n"
+        "L.fcirc_debug_fail_alloc(-1)\n"
+        "print(rc, L.fcirc_sync_status(None))\n")
+    r = subprocess.run([sys.executable, "-c", code], cwd=root, capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stderr[-2000:]
+    assert r.stdout.split()[-2:] == ["3", "0"], r.stdout

@@ -201,3 +201,14 @@ def test_gf_roots(F):
     assert _gf_root(F, g, 1)[0] == 2
     assert _gf_root(F, (0, 0), 3)[0] == 2
     assert _gf_root(F, (GFP, 0), 3)[0] == 1
+
+
+def test_mul_probe_rejects_bad_arguments_before_any_device_call(F):
+    import ctypes as C
+    L = F.load()
+    ms, rate = C.c_double(), C.c_double()
+    assert L.fcirc_prof_mul_probe(2, 4, 16, C.byref(ms), C.byref(rate)) == 1     # kind
+    assert L.fcirc_prof_mul_probe(0, 0, 16, C.byref(ms), C.byref(rate)) == 1     # no CTAs
+    assert L.fcirc_prof_mul_probe(0, 9, 16, C.byref(ms), C.byref(rate)) == 1     # too many
+    assert L.fcirc_prof_mul_probe(0, 4, 0, C.byref(ms), C.byref(rate)) == 1      # no work
+    assert L.fcirc_prof_mul_probe(0, 4, 16, None, C.byref(rate)) == 1
