@@ -174,23 +174,37 @@ struct FwdDesc {
     int half;
 };
 
-int run_fwd_pass(int pass, const FwdDesc *jd, int njobs, int jobs_per_cta, cudaStream_t s)
+// The register-staged column pass parameters of forward pass `pass`; false
+// when the pass's shape needs the generic strided kernels.
+bool fwd_params(int pass, const FwdDesc *jd, int njobs, int jobs_per_cta, ColFwdParams &P)
 {
     const Plan &sh = *jd[0].pl;
     const int l0 = sh.pass_l0[pass], l1 = sh.pass_l1[pass];
-    if (fast_col_ok(l1 - l0, sh.m - l1)) {
-        ColFwdParams P{};
-        for (int k = 0; k < njobs; ++k)
-            P.job[k] = ColFwdJob{jd[k].src, jd[k].dst, jd[k].pl->d_gtw + jd[k].pl->pass_goff[pass],
-                                 jd[k].pl->p, jd[k].vec_side, jd[k].half};
-        P.jobs_per_cta = jobs_per_cta;
-        P.N = (uint32_t)sh.n;
-        P.logn = sh.m;
-        P.l0 = l0;
-        P.l1 = l1;
-        for (int st = 0; st < 3; ++st) P.stage_off[st] = sh.stage_off[pass][st];
-        return launch_colfwd(P, njobs / jobs_per_cta, s);
+    if (!fast_col_ok(l1 - l0, sh.m - l1)) return false;
+    P = ColFwdParams{};
+    for (int k = 0; k < njobs; ++k)
+        P.job[k] = ColFwdJob{jd[k].src, jd[k].dst, jd[k].pl->d_gtw + jd[k].pl->pass_goff[pass], jd[k].pl->p,
+                             jd[k].vec_side, jd[k].half};
+    P.jobs_per_cta = jobs_per_cta;
+    P.N = (uint32_t)sh.n;
+    P.logn = sh.m;
+    P.l0 = l0;
+    P.l1 = l1;
+    for (int st = 0; st < 3; ++st) P.stage_off[st] = sh.stage_off[pass][st];
+    return true;
+}
+
+// ilv: write the tile-pair interleaved layout (tiles_ilv_ok said yes)
+int run_fwd_pass(int pass, const FwdDesc *jd, int njobs, int jobs_per_cta, cudaStream_t s, int ilv = 0)
+{
+    const Plan &sh = *jd[0].pl;
+    const int l0 = sh.pass_l0[pass], l1 = sh.pass_l1[pass];
+    ColFwdParams CP;
+    if (fwd_params(pass, jd, njobs, jobs_per_cta, CP)) {
+        CP.ilv = ilv;
+        return launch_colfwd(CP, njobs / jobs_per_cta, s);
     }
+    if (ilv) return fail(FCIRC_EINVAL, "interleaved layout requested from a strided pass");
     StrFwdParams P{};
     for (int k = 0; k < njobs; ++k)
         P.job[k] = StrFwdJob{jd[k].src, jd[k].dst, jd[k].pl->d_ftw, jd[k].pl->p, jd[k].vec_side};
@@ -208,27 +222,40 @@ struct InvDesc {
     const Plan *pl;
 };
 
-int run_inv_pass(int pass, const InvDesc *jd, int nprime, int epi, uint64_t *dst64, uint64_t nout,
-                 const CrtConsts *crt, cudaStream_t s)
+bool inv_params(int pass, const InvDesc *jd, int nprime, int epi, uint64_t *dst64, uint64_t nout,
+                const CrtConsts *crt, ColInvParams &P)
 {
     const Plan &sh = *jd[0].pl;
     const int l0 = sh.pass_l0[pass], l1 = sh.pass_l1[pass];
-    if (fast_col_ok(l1 - l0, sh.m - l1)) {
-        ColInvParams P{};
-        for (int q = 0; q < nprime; ++q)
-            P.job[q] = ColInvJob{jd[q].src, jd[q].dst, jd[q].pl->d_gitw + jd[q].pl->pass_goff[pass], jd[q].pl->p};
-        P.nprime = nprime;
-        P.N = (uint32_t)sh.n;
-        P.logn = sh.m;
-        P.l0 = l0;
-        P.l1 = l1;
-        for (int st = 0; st < 3; ++st) P.stage_off[st] = sh.stage_off[pass][st];
-        P.epi = epi;
-        P.dst64 = dst64;
-        P.nout = nout;
-        if (crt) P.crt = *crt;
-        return launch_colinv(P, s);
+    if (!fast_col_ok(l1 - l0, sh.m - l1)) return false;
+    P = ColInvParams{};
+    for (int q = 0; q < nprime; ++q)
+        P.job[q] = ColInvJob{jd[q].src, jd[q].dst, jd[q].pl->d_gitw + jd[q].pl->pass_goff[pass], jd[q].pl->p};
+    P.nprime = nprime;
+    P.N = (uint32_t)sh.n;
+    P.logn = sh.m;
+    P.l0 = l0;
+    P.l1 = l1;
+    for (int st = 0; st < 3; ++st) P.stage_off[st] = sh.stage_off[pass][st];
+    P.epi = epi;
+    P.dst64 = dst64;
+    P.nout = nout;
+    if (crt) P.crt = *crt;
+    return true;
+}
+
+// ilv: read the tile-pair interleaved layout (tiles_ilv_ok said yes)
+int run_inv_pass(int pass, const InvDesc *jd, int nprime, int epi, uint64_t *dst64, uint64_t nout,
+                 const CrtConsts *crt, cudaStream_t s, int ilv = 0)
+{
+    const Plan &sh = *jd[0].pl;
+    const int l0 = sh.pass_l0[pass], l1 = sh.pass_l1[pass];
+    ColInvParams CP;
+    if (inv_params(pass, jd, nprime, epi, dst64, nout, crt, CP)) {
+        CP.ilv = ilv;
+        return launch_colinv(CP, s);
     }
+    if (ilv) return fail(FCIRC_EINVAL, "interleaved layout requested from a strided pass");
     StrInvParams P{};
     for (int q = 0; q < nprime; ++q) P.job[q] = StrInvJob{jd[q].src, jd[q].dst, jd[q].pl->d_fitw, jd[q].pl->p};
     P.nprime = nprime;
@@ -245,6 +272,29 @@ int run_inv_pass(int pass, const InvDesc *jd, int nprime, int epi, uint64_t *dst
 }
 
 Src src_u32(const void *ptr, uint64_t n) { return Src{ptr, n, SRC_U32, 0, Tw{0, 0}}; }
+
+// Whether the arrays between the last forward column pass, the 4096-residue
+// tiles and the first inverse column pass can take the tile-pair interleaved
+// layout (ilv_pos): the four-column kernels run both passes and the tile
+// kernel is the register-staged one.  `fwd` and `inv` describe the last
+// forward pass (index npass - 1) and the first inverse pass (the same index).
+bool tiles_ilv_ok(const Plan &pl, const FwdDesc *fwd, int njobs, int jobs_per_cta, const InvDesc *inv, int nprime,
+                  int epi, uint64_t *dst64, uint64_t nout, const CrtConsts *crt)
+{
+    if (pl.k == 0 || pl.npass < 1 || !fast_tile_ok(pl.logT)) return false;
+    ColFwdParams F;
+    ColInvParams I;
+    const int last = pl.npass - 1;
+    if (!fwd_params(last, fwd, njobs, jobs_per_cta, F) || !inv_params(last, inv, nprime, epi, dst64, nout, crt, I))
+        return false;
+    // an interleaved array cannot be recombined in place: the natural
+    // positions a column group writes hold interleaved residues of other
+    // column groups, which other CTAs may not have read yet
+    if (!epi_crt(epi))
+        for (int q = 0; q < nprime; ++q)
+            if (inv[q].src == inv[q].dst) return false;
+    return col4_fwd_ilv_ok(F, njobs / jobs_per_cta) && col4_inv_ilv_ok(I);
+}
 
 }  // namespace
 
@@ -263,22 +313,35 @@ static int matvec_core(const Plan *pl, const Src &sa, const Src &sx, uint32_t *d
         tp.D = pl->D;
         return run_tile(tp, 1, 1, s);
     }
+    auto fwd_desc = [&](int i, FwdDesc *jd) {
+        jd[0] = FwdDesc{i == 0 ? sa : src_u32(dc, n), dc, pl, 0, 0};
+        jd[1] = FwdDesc{i == 0 ? sx : src_u32(xs, n), xs, pl, 1, 0};
+    };
+    // the tiles leave their products in xs; the first recombination pass
+    // reads them there and writes c, the others work in place in c
+    const int last = pl->npass - 1;
+    auto inv_desc = [&](int i) { return InvDesc{i == last ? xs : dc, dc, pl}; };
+    FwdDesc ljd[2];
+    fwd_desc(last, ljd);
+    const InvDesc lid[1] = {inv_desc(last)};
+    const int ilv = tiles_ilv_ok(*pl, ljd, 2, 1, lid, 1, last == 0 ? EPI_CANON : EPI_LAZY, nullptr, 0, nullptr);
     for (int i = 0; i < pl->npass; ++i) {
-        FwdDesc jd[2] = {FwdDesc{i == 0 ? sa : src_u32(dc, n), dc, pl, 0, 0},
-                         FwdDesc{i == 0 ? sx : src_u32(xs, n), xs, pl, 1, 0}};
-        FCIRC_TRY(run_fwd_pass(i, jd, 2, 1, s));
+        FwdDesc jd[2];
+        fwd_desc(i, jd);
+        FCIRC_TRY(run_fwd_pass(i, jd, 2, 1, s, i == last ? ilv : 0));
     }
     {
         TileParams tp;
-        tp.job[0] = tile_job(pl, src_u32(dc, n), src_u32(xs, n), dc, 1);
+        tp.job[0] = tile_job(pl, src_u32(dc, n), src_u32(xs, n), xs, 1);
         tp.N = n;
         tp.logT = pl->logT;
         tp.D = pl->D;
+        tp.ilv = ilv ? 3 : 0;
         FCIRC_TRY(run_tile(tp, (uint64_t)1 << pl->k, 1, s));
     }
-    for (int i = pl->npass - 1; i >= 0; --i) {
-        InvDesc jd[1] = {InvDesc{dc, dc, pl}};
-        FCIRC_TRY(run_inv_pass(i, jd, 1, i == 0 ? EPI_CANON : EPI_LAZY, nullptr, 0, nullptr, s));
+    for (int i = last; i >= 0; --i) {
+        const InvDesc jd[1] = {inv_desc(i)};
+        FCIRC_TRY(run_inv_pass(i, jd, 1, i == 0 ? EPI_CANON : EPI_LAZY, nullptr, 0, nullptr, s, i == last ? ilv : 0));
     }
     return FCIRC_OK;
 }
@@ -351,8 +414,7 @@ static int poly_core(const uint16_t *P, uint64_t np, const uint16_t *Q, uint64_t
         FCIRC_TRY(run_tile(tp, 1, 3, s));
         return launch_crt_rot(A[0], A[1], A[2], N, out, nout, crt, s);
     }
-    for (int i = 0; i < p0.npass; ++i) {
-        FwdDesc jd[6];
+    auto fwd_desc = [&](int i, FwdDesc *jd) {
         // f = 1 gives s = 1 at level 0; with both inputs shorter than N/2 that
         // level only copies (row vector zero below N/2, vector from N/2)
         const int half = (np <= N / 2 && nq <= N / 2) ? 1 : 0;
@@ -365,14 +427,25 @@ static int poly_core(const uint16_t *P, uint64_t np, const uint16_t *Q, uint64_t
                 jd[3 + q] = FwdDesc{src_u32(X[q], N), X[q], pl[q], 1, 0};
             }
         }
-        FCIRC_TRY(run_fwd_pass(i, jd, 6, 3, s));
-    }
+    };
     // The reversed-row embedding moves the product up by one entry
     // (coefficient k is circulant entry k + 1).  The 4096-residue tile kernel
     // undoes that in its leaves (TILE_SHIFT: the row vector shifted by one
     // place, an identity at f = 1), so the CRT writes whole aligned sectors;
     // the other tile kernels leave it to the CRT (EPI_CRT_ROT).
     const bool shift = fast_tile_ok(p0.logT);
+    InvDesc ijd[3];
+    for (int q = 0; q < 3; ++q) ijd[q] = InvDesc{A[q], A[q], pl[q]};
+    const int last = p0.npass - 1;
+    auto epi_of = [&](int i) { return i == 0 ? (shift ? EPI_CRT : EPI_CRT_ROT) : EPI_LAZY; };
+    FwdDesc ljd[6];
+    fwd_desc(last, ljd);
+    const int ilv = tiles_ilv_ok(p0, ljd, 6, 3, ijd, 3, epi_of(last), out, nout, &crt);
+    for (int i = 0; i < p0.npass; ++i) {
+        FwdDesc jd[6];
+        fwd_desc(i, jd);
+        FCIRC_TRY(run_fwd_pass(i, jd, 6, 3, s, i == last ? ilv : 0));
+    }
     {
         TileParams tp;
         for (int q = 0; q < 3; ++q) tp.job[q] = tile_job(pl[q], src_u32(A[q], N), src_u32(X[q], N), A[q], 1);
@@ -380,13 +453,11 @@ static int poly_core(const uint16_t *P, uint64_t np, const uint16_t *Q, uint64_t
         tp.logT = p0.logT;
         tp.D = p0.D;
         tp.var = shift ? TILE_SHIFT : TILE_FULL;
+        tp.ilv = ilv ? 3 : 0;
         FCIRC_TRY(run_tile(tp, (uint64_t)1 << p0.k, 3, s));
     }
-    for (int i = p0.npass - 1; i >= 0; --i) {
-        InvDesc jd[3];
-        for (int q = 0; q < 3; ++q) jd[q] = InvDesc{A[q], A[q], pl[q]};
-        FCIRC_TRY(run_inv_pass(i, jd, 3, i == 0 ? (shift ? EPI_CRT : EPI_CRT_ROT) : EPI_LAZY, out, nout, &crt, s));
-    }
+    for (int i = last; i >= 0; --i)
+        FCIRC_TRY(run_inv_pass(i, ijd, 3, epi_of(i), out, nout, &crt, s, i == last ? ilv : 0));
     return FCIRC_OK;
 }
 
@@ -607,10 +678,20 @@ int fcirc_matvec_aplan(fcirc_aplan_t h, const uint32_t *x, uint32_t *c, void *st
     }
     // the vector's tree in the scratch, the tiles (transformed row vector
     // read as it is) in place there, and the recombination into c
+    // (the vector side and the tile output may take the interleaved layout;
+    // the transformed row vector keeps the tile kernel's own layout)
     uint32_t *xs = reinterpret_cast<uint32_t *>(st.scratch);
+    const int last = pl->npass - 1;
+    auto fjd = [&](int i) { return FwdDesc{i == 0 ? sx : src_u32(xs, n), xs, pl, 1, 0}; };
+    // the first recombination pass reads the tiles' products in xs and
+    // writes c; the others work in place in c
+    auto ijd = [&](int i) { return InvDesc{i == last ? xs : dc, dc, pl}; };
+    const FwdDesc lf[1] = {fjd(last)};
+    const InvDesc li[1] = {ijd(last)};
+    const int ilv = tiles_ilv_ok(*pl, lf, 1, 1, li, 1, last == 0 ? EPI_CANON : EPI_LAZY, nullptr, 0, nullptr);
     for (int i = 0; i < pl->npass; ++i) {
-        FwdDesc jd[1] = {FwdDesc{i == 0 ? sx : src_u32(xs, n), xs, pl, 1, 0}};
-        FCIRC_TRY(run_fwd_pass(i, jd, 1, 1, s));
+        FwdDesc jd[1] = {fjd(i)};
+        FCIRC_TRY(run_fwd_pass(i, jd, 1, 1, s, i == last ? ilv : 0));
     }
     {
         TileParams tp;
@@ -619,11 +700,13 @@ int fcirc_matvec_aplan(fcirc_aplan_t h, const uint32_t *x, uint32_t *c, void *st
         tp.logT = pl->logT;
         tp.D = pl->D;
         tp.var = TILE_PLANNED;
+        tp.ilv = ilv ? 2 : 0;
         FCIRC_TRY(run_tile(tp, (uint64_t)1 << pl->k, 1, s));
     }
-    for (int i = pl->npass - 1; i >= 0; --i) {
-        InvDesc jd[1] = {InvDesc{xs, i == 0 ? dc : xs, pl}};
-        FCIRC_TRY(run_inv_pass(i, jd, 1, i == 0 ? EPI_CANON : EPI_LAZY, nullptr, 0, nullptr, s));
+    for (int i = last; i >= 0; --i) {
+        InvDesc jd[1] = {ijd(i)};
+        FCIRC_TRY(run_inv_pass(i, jd, 1, i == 0 ? EPI_CANON : EPI_LAZY, nullptr, 0, nullptr, s,
+                               i == last ? ilv : 0));
     }
     return st.end();
 }

@@ -359,6 +359,28 @@ __device__ __forceinline__ void c4_rec(uint32_t *v, const Tw *g, const Tw *cur, 
     }
 }
 
+// One 32-byte sector: eight consecutive words of the tile-pair interleaved
+// layout (a column quad of two adjacent rows), from or to v[0..8).
+__device__ __forceinline__ void st_sector(uint32_t *d, const uint32_t *v)
+{
+    asm volatile("st.global.v4.u64 [%0], {%1, %2, %3, %4};\n" ::"l"(d),
+                 "l"((uint64_t)v[0] | ((uint64_t)v[1] << 32)), "l"((uint64_t)v[2] | ((uint64_t)v[3] << 32)),
+                 "l"((uint64_t)v[4] | ((uint64_t)v[5] << 32)), "l"((uint64_t)v[6] | ((uint64_t)v[7] << 32))
+                 : "memory");
+}
+
+__device__ __forceinline__ void ld_sector(const uint32_t *s, uint32_t *v)
+{
+    uint64_t w0, w1, w2, w3;
+    asm volatile("ld.global.nc.v4.u64 {%0, %1, %2, %3}, [%4];\n"
+                 : "=l"(w0), "=l"(w1), "=l"(w2), "=l"(w3)
+                 : "l"(s));
+    v[0] = (uint32_t)w0; v[1] = (uint32_t)(w0 >> 32);
+    v[2] = (uint32_t)w1; v[3] = (uint32_t)(w1 >> 32);
+    v[4] = (uint32_t)w2; v[5] = (uint32_t)(w2 >> 32);
+    v[6] = (uint32_t)w3; v[7] = (uint32_t)(w3 >> 32);
+}
+
 __device__ __forceinline__ void put4(uint32_t *v, uint4 w)
 {
     v[0] = w.x;
@@ -369,7 +391,9 @@ __device__ __forceinline__ void put4(uint32_t *v, uint4 w)
 
 __device__ __forceinline__ uint4 get4(const uint32_t *v) { return make_uint4(v[0], v[1], v[2], v[3]); }
 
-template <int LF, int S, int MODE, bool VEC>
+// ILV: the pass writes the tile-pair interleaved layout; its last stage
+// stores straight from registers (no shared-memory write, no store phase).
+template <int LF, int S, int MODE, bool VEC, bool ILV>
 __device__ __forceinline__ void c4fwd_stage(const ColFwdJob &J, const ColFwdParams &P, uint32_t *sm,
                                             uint32_t base, uint32_t pb, int logS, int tid, bool wait_first,
                                             int cache = C4_NOCACHE)
@@ -447,8 +471,26 @@ __device__ __forceinline__ void c4fwd_stage(const ColFwdJob &J, const ColFwdPara
         }
         c4_fwd<NL, DS, VEC>(vg, g, t0, p, p2);
     }
-    // the previous job's store phase may still read this CTA's shared memory
-    if (FIRST && wait_first) grp_wait<Sh::CL>();
+    if constexpr (ILV && S == Sh::NST - 1) {
+        // the last stage holds 16 consecutive rows (tiles) of one column
+        // quad; row pair k is one sector of the interleaved layout, and the
+        // pass has 2^12 columns (col4_fwd_ilv_ok), so rows are 2^12 apart
+        static_assert(B == 1 && M == 16 && LST == 0, "last stage shape");
+        int quad, row0, blk;
+        c4_group<LF, D0, NL>(tid, 0, quad, row0, blk);
+        uint32_t *d = J.dst + ilv_pos(base + ((uint32_t)quad << 2) + ((uint32_t)row0 << 12));
+#pragma unroll
+        for (int k = 0; k < 8; ++k) st_sector(d + 8192 * k, v + 8 * k);
+        return;
+    }
+    // the previous job's last stage (or store phase) may still read this
+    // CTA's shared memory
+    if (FIRST && wait_first) {
+        if constexpr (ILV)
+            __syncthreads();
+        else
+            grp_wait<Sh::CL>();
+    }
 #pragma unroll
     for (int hb = 0; hb < B; ++hb) {
         int quad, row0, blk;
@@ -459,37 +501,39 @@ __device__ __forceinline__ void c4fwd_stage(const ColFwdJob &J, const ColFwdPara
     }
 }
 
-template <int LF, int MODE, bool VEC>
+template <int LF, int MODE, bool VEC, bool ILV>
 __device__ __forceinline__ void c4fwd_jobs(const ColFwdParams &P, uint32_t *sm, int j0, uint32_t base,
                                            uint32_t pb, int logS, int tid)
 {
     using Sh = C4<LF>;
-    const int rank = Sh::CL > 1 ? (int)cl_rank() : 0;
+    const int rank = (!ILV && Sh::CL > 1) ? (int)cl_rank() : 0;
     const uint32_t base0 = base - ((uint32_t)rank << (2 + Sh::LNQ));
     const bool cached = C4Cache<MODE>::ON && P.share_src && P.jobs_per_cta > 1;
 #pragma unroll 1
     for (int jj = 0; jj < P.jobs_per_cta; ++jj) {
         const ColFwdJob &J = P.job[j0 + jj];
-        c4fwd_stage<LF, 0, MODE, VEC>(J, P, sm, base, pb, logS, tid, jj > 0,
-                                      cached ? (jj == 0 ? C4_FILL : C4_USE) : C4_NOCACHE);
+        c4fwd_stage<LF, 0, MODE, VEC, ILV>(J, P, sm, base, pb, logS, tid, jj > 0,
+                                           cached ? (jj == 0 ? C4_FILL : C4_USE) : C4_NOCACHE);
         if constexpr (Sh::NST > 1) {
             __syncthreads();
-            c4fwd_stage<LF, 1, MODE, VEC>(J, P, sm, base, pb, logS, tid, false);
+            c4fwd_stage<LF, 1, MODE, VEC, ILV>(J, P, sm, base, pb, logS, tid, false);
         }
         if constexpr (Sh::NST > 2) {
             __syncthreads();
-            c4fwd_stage<LF, 2, MODE, VEC>(J, P, sm, base, pb, logS, tid, false);
+            c4fwd_stage<LF, 2, MODE, VEC, ILV>(J, P, sm, base, pb, logS, tid, false);
         }
         if constexpr (Sh::NST > 3) {
             __syncthreads();
-            c4fwd_stage<LF, 3, MODE, VEC>(J, P, sm, base, pb, logS, tid, false);
+            c4fwd_stage<LF, 3, MODE, VEC, ILV>(J, P, sm, base, pb, logS, tid, false);
         }
-        grp_arrive<Sh::CL>();
-        grp_wait<Sh::CL>();
-        c4_store_phase<LF>(sm, J.dst, base0, logS, rank, tid);
-        grp_arrive_done<Sh::CL>();
+        if constexpr (!ILV) {
+            grp_arrive<Sh::CL>();
+            grp_wait<Sh::CL>();
+            c4_store_phase<LF>(sm, J.dst, base0, logS, rank, tid);
+            grp_arrive_done<Sh::CL>();
+        }
     }
-    grp_wait<Sh::CL>();   // no CTA leaves while a peer still reads its shared memory
+    if constexpr (!ILV) grp_wait<Sh::CL>();   // no CTA leaves while a peer still reads its shared memory
 }
 
 // CTA origin: node pb of level l0 and the CTA's first column
@@ -504,8 +548,9 @@ __device__ __forceinline__ void c4_origin(int logn, int l0, int l1, uint32_t &pb
     base = (pb << (logn - l0)) + (cg << (2 + C4<LF>::LNQ));
 }
 
-template <int LF, int M0, int M1>
-__global__ void __cluster_dims__(C4<LF>::CL, 1, 1) __launch_bounds__(kC4Threads, FCIRC_C4FWD_MINB) k_colfwd4(const __grid_constant__ ColFwdParams P)
+template <int LF, int M0, int M1, bool ILV>
+__global__ void __cluster_dims__(ILV ? 1 : C4<LF>::CL, 1, 1) __launch_bounds__(kC4Threads, FCIRC_C4FWD_MINB)
+    k_colfwd4(const __grid_constant__ ColFwdParams P)
 {
     extern __shared__ __align__(16) uint32_t sm[];
     uint32_t pb, base;
@@ -515,13 +560,15 @@ __global__ void __cluster_dims__(C4<LF>::CL, 1, 1) __launch_bounds__(kC4Threads,
     // job groups below vec_group0 are the row-vector side, the rest the
     // vector side
     if ((int)blockIdx.y < P.vec_group0)
-        c4fwd_jobs<LF, M0, false>(P, sm, j0, base, pb, logS, threadIdx.x);
+        c4fwd_jobs<LF, M0, false, ILV>(P, sm, j0, base, pb, logS, threadIdx.x);
     else
-        c4fwd_jobs<LF, M1, true>(P, sm, j0, base, pb, logS, threadIdx.x);
+        c4fwd_jobs<LF, M1, true, ILV>(P, sm, j0, base, pb, logS, threadIdx.x);
 }
 
 // Stage S of the recombination for one prime's job J, its residues in smq.
-template <int LF, int S>
+// ILV: the pass reads the tile-pair interleaved layout; its first stage
+// loads whole 32-byte sectors (a column quad of two adjacent rows).
+template <int LF, int S, bool ILV>
 __device__ __forceinline__ void c4inv_job(const ColInvParams &P, const ColInvJob &J, uint32_t *smq, uint32_t base,
                                           uint32_t pb, int logS, int tid)
 {
@@ -533,20 +580,31 @@ __device__ __forceinline__ void c4inv_job(const ColInvParams &P, const ColInvJob
         const uint32_t p = J.p, p2 = 2 * J.p;
         const Tw *gt = J.gitw + P.stage_off[S];
         uint32_t v[4 * kC4Rows];
-#pragma unroll
-        for (int hb = 0; hb < B; ++hb) {
+        if constexpr (FIRST && ILV) {
+            // 16 consecutive rows (tiles) of one quad, 2^12 columns
+            // (col4_inv_ilv_ok): eight sectors of row pairs
+            static_assert(B == 1 && M == 16 && LST == 0, "first stage shape");
             int quad, row0, blk;
-            c4_group<LF, D0, NL>(tid, hb, quad, row0, blk);
+            c4_group<LF, D0, NL>(tid, 0, quad, row0, blk);
+            const uint32_t *src = J.src + ilv_pos(base + ((uint32_t)quad << 2) + ((uint32_t)row0 << 12));
 #pragma unroll
-            for (int i = 0; i < M; ++i) {
-                const int row = row0 + (i << LST);
-                uint4 w;
-                if constexpr (FIRST)
-                    w = __ldg(reinterpret_cast<const uint4 *>(J.src + base + ((uint32_t)quad << 2) +
-                                                              ((uint32_t)row << logS)));
-                else
-                    w = *reinterpret_cast<const uint4 *>(smq + C4Addr<LF, LST>(quad, row0)(i));
-                put4(v + 4 * (hb * M + i), w);
+            for (int k = 0; k < 8; ++k) ld_sector(src + 8192 * k, v + 8 * k);
+        } else {
+#pragma unroll
+            for (int hb = 0; hb < B; ++hb) {
+                int quad, row0, blk;
+                c4_group<LF, D0, NL>(tid, hb, quad, row0, blk);
+#pragma unroll
+                for (int i = 0; i < M; ++i) {
+                    const int row = row0 + (i << LST);
+                    uint4 w;
+                    if constexpr (FIRST)
+                        w = __ldg(reinterpret_cast<const uint4 *>(J.src + base + ((uint32_t)quad << 2) +
+                                                                  ((uint32_t)row << logS)));
+                    else
+                        w = *reinterpret_cast<const uint4 *>(smq + C4Addr<LF, LST>(quad, row0)(i));
+                    put4(v + 4 * (hb * M + i), w);
+                }
             }
         }
 #pragma unroll
@@ -577,12 +635,12 @@ __device__ __forceinline__ void c4inv_job(const ColInvParams &P, const ColInvJob
     }
 }
 
-template <int LF, int NP, int S>
+template <int LF, int NP, int S, bool ILV>
 __device__ __forceinline__ void c4inv_stage(const ColInvParams &P, uint32_t *sm, uint32_t base, uint32_t pb,
                                             int logS, int tid)
 {
 #pragma unroll 1
-    for (int q = 0; q < NP; ++q) c4inv_job<LF, S>(P, P.job[q], sm + q * C4<LF>::WORDS, base, pb, logS, tid);
+    for (int q = 0; q < NP; ++q) c4inv_job<LF, S, ILV>(P, P.job[q], sm + q * C4<LF>::WORDS, base, pb, logS, tid);
 }
 
 // The CRT of one quad (circulant entries idx .. idx+3, the three primes'
@@ -648,7 +706,7 @@ __device__ __forceinline__ void c4_crt_phase(const ColInvParams &P, const uint32
     }
 }
 
-template <int LF, int NP>
+template <int LF, int NP, bool ILV>
 __global__ void __cluster_dims__(C4<LF>::CL, 1, 1) __launch_bounds__(kC4Threads, NP == 1 ? FCIRC_C4INV_MINB : 1)
     k_colinv4(const __grid_constant__ ColInvParams P)
 {
@@ -661,18 +719,18 @@ __global__ void __cluster_dims__(C4<LF>::CL, 1, 1) __launch_bounds__(kC4Threads,
     const int rank = Sh::CL > 1 ? (int)cl_rank() : 0;
     const uint32_t base0 = base - ((uint32_t)rank << (2 + Sh::LNQ));
     if constexpr (Sh::NST > 3) {
-        c4inv_stage<LF, NP, 3>(P, sm, base, pb, logS, tid);
+        c4inv_stage<LF, NP, 3, ILV>(P, sm, base, pb, logS, tid);
         __syncthreads();
     }
     if constexpr (Sh::NST > 2) {
-        c4inv_stage<LF, NP, 2>(P, sm, base, pb, logS, tid);
+        c4inv_stage<LF, NP, 2, ILV>(P, sm, base, pb, logS, tid);
         __syncthreads();
     }
     if constexpr (Sh::NST > 1) {
-        c4inv_stage<LF, NP, 1>(P, sm, base, pb, logS, tid);
+        c4inv_stage<LF, NP, 1, ILV>(P, sm, base, pb, logS, tid);
         __syncthreads();
     }
-    c4inv_stage<LF, NP, 0>(P, sm, base, pb, logS, tid);
+    c4inv_stage<LF, NP, 0, ILV>(P, sm, base, pb, logS, tid);
     grp_arrive<Sh::CL>();
     grp_wait<Sh::CL>();
     if (NP == 3 && epi_crt(P.epi)) {
@@ -692,7 +750,7 @@ __global__ void __cluster_dims__(C4<LF>::CL, 1, 1) __launch_bounds__(kC4Threads,
 // and arithmetic phases); then each CTA takes a third of the group's rows,
 // gathers the three canonical residues through distributed shared memory,
 // and writes the CRT results (crt_store4).
-template <int LF>
+template <int LF, bool ILV>
 __global__ void __cluster_dims__(3, 1, 1) __launch_bounds__(kC4Threads, 2)
     k_colinv4x3(const __grid_constant__ ColInvParams P)
 {
@@ -705,18 +763,18 @@ __global__ void __cluster_dims__(3, 1, 1) __launch_bounds__(kC4Threads, 2)
     const int tid = threadIdx.x;
     const ColInvJob &J = P.job[q];
     if constexpr (Sh::NST > 3) {
-        c4inv_job<LF, 3>(P, J, sm, base, pb, logS, tid);
+        c4inv_job<LF, 3, ILV>(P, J, sm, base, pb, logS, tid);
         __syncthreads();
     }
     if constexpr (Sh::NST > 2) {
-        c4inv_job<LF, 2>(P, J, sm, base, pb, logS, tid);
+        c4inv_job<LF, 2, ILV>(P, J, sm, base, pb, logS, tid);
         __syncthreads();
     }
     if constexpr (Sh::NST > 1) {
-        c4inv_job<LF, 1>(P, J, sm, base, pb, logS, tid);
+        c4inv_job<LF, 1, ILV>(P, J, sm, base, pb, logS, tid);
         __syncthreads();
     }
-    c4inv_job<LF, 0>(P, J, sm, base, pb, logS, tid);
+    c4inv_job<LF, 0, ILV>(P, J, sm, base, pb, logS, tid);
     cl_arrive();
     cl_wait();   // all three primes' residues are in place
     constexpr int W = 1 << 12;                   // 16-byte words (quad, row) per CTA
@@ -760,12 +818,12 @@ bool src_aligned(const Src &s)
     return (s.kind == SRC_U32 || s.kind == SRC_U32_REV) ? aligned(s.ptr, 16) : aligned(s.ptr, 8);
 }
 
-template <int LF, int M0, int M1>
+template <int LF, int M0, int M1, bool ILV>
 int launch_c4fwd_m(const ColFwdParams &P, int nctay, cudaStream_t s)
 {
     static std::atomic<unsigned> mask{0};
     constexpr int cache_max = C4Cache<M0>::BYTES > C4Cache<M1>::BYTES ? C4Cache<M0>::BYTES : C4Cache<M1>::BYTES;
-    FCIRC_TRY(c4_smem(k_colfwd4<LF, M0, M1>, C4<LF>::WORDS * 4 + cache_max, mask));
+    FCIRC_TRY(c4_smem(k_colfwd4<LF, M0, M1, ILV>, C4<LF>::WORDS * 4 + cache_max, mask));
     const uint64_t ncta = (uint64_t)1 << (P.l0 + (P.logn - P.l1) - 2 - C4<LF>::LNQ);
     // optionally one job per CTA (more, shorter CTAs)
     ColFwdParams P1 = P;
@@ -784,31 +842,56 @@ int launch_c4fwd_m(const ColFwdParams &P, int nctay, cudaStream_t s)
     }
     dim3 grid((unsigned)ncta, ny);
     ProfScope ps("k_colfwd4", s);
-    k_colfwd4<LF, M0, M1><<<grid, kC4Threads, smem, s>>>(P1);
+    k_colfwd4<LF, M0, M1, ILV><<<grid, kC4Threads, smem, s>>>(P1);
     FCIRC_CUDA_TRY(cudaGetLastError());
     return FCIRC_OK;
+}
+
+template <int LF, bool ILV>
+int launch_c4fwd_lf(const ColFwdParams &P, int nctay, int m0, int m1, cudaStream_t s)
+{
+    if (m0 == MODE_U32_S && m1 == MODE_U32) return launch_c4fwd_m<LF, MODE_U32_S, MODE_U32, ILV>(P, nctay, s);
+    if (m0 == MODE_U32REV_S && m1 == MODE_U32) return launch_c4fwd_m<LF, MODE_U32REV_S, MODE_U32, ILV>(P, nctay, s);
+    if (m0 == MODE_U32 && m1 == MODE_U32) return launch_c4fwd_m<LF, MODE_U32, MODE_U32, ILV>(P, nctay, s);
+    if (m0 == MODE_REV_S_H && m1 == MODE_U16_H) return launch_c4fwd_m<LF, MODE_REV_S_H, MODE_U16_H, ILV>(P, nctay, s);
+    if (m0 == MODE_REV_S && m1 == MODE_U16) return launch_c4fwd_m<LF, MODE_REV_S, MODE_U16, ILV>(P, nctay, s);
+    return fail(FCIRC_EINVAL, "column pass: unsupported source modes %d/%d", m0, m1);
 }
 
 template <int LF>
 int launch_c4fwd_lf(const ColFwdParams &P, int nctay, int m0, int m1, cudaStream_t s)
 {
-    if (m0 == MODE_U32_S && m1 == MODE_U32) return launch_c4fwd_m<LF, MODE_U32_S, MODE_U32>(P, nctay, s);
-    if (m0 == MODE_U32REV_S && m1 == MODE_U32) return launch_c4fwd_m<LF, MODE_U32REV_S, MODE_U32>(P, nctay, s);
-    if (m0 == MODE_U32 && m1 == MODE_U32) return launch_c4fwd_m<LF, MODE_U32, MODE_U32>(P, nctay, s);
-    if (m0 == MODE_REV_S_H && m1 == MODE_U16_H) return launch_c4fwd_m<LF, MODE_REV_S_H, MODE_U16_H>(P, nctay, s);
-    if (m0 == MODE_REV_S && m1 == MODE_U16) return launch_c4fwd_m<LF, MODE_REV_S, MODE_U16>(P, nctay, s);
-    return fail(FCIRC_EINVAL, "column pass: unsupported source modes %d/%d", m0, m1);
+    return P.ilv ? launch_c4fwd_lf<LF, true>(P, nctay, m0, m1, s) : launch_c4fwd_lf<LF, false>(P, nctay, m0, m1, s);
+}
+
+template <int LF, int NP, bool ILV>
+int launch_c4inv_lf_(const ColInvParams &P, cudaStream_t s)
+{
+    static std::atomic<unsigned> mask{0};
+    const int smem = NP * C4<LF>::WORDS * 4;
+    FCIRC_TRY(c4_smem(k_colinv4<LF, NP, ILV>, smem, mask));
+    const uint64_t ncta = (uint64_t)1 << (P.l0 + (P.logn - P.l1) - 2 - C4<LF>::LNQ);
+    ProfScope ps("k_colinv4", s);
+    k_colinv4<LF, NP, ILV><<<(unsigned)ncta, kC4Threads, smem, s>>>(P);
+    FCIRC_CUDA_TRY(cudaGetLastError());
+    return FCIRC_OK;
 }
 
 template <int LF, int NP>
 int launch_c4inv_lf(const ColInvParams &P, cudaStream_t s)
 {
+    return P.ilv ? launch_c4inv_lf_<LF, NP, true>(P, s) : launch_c4inv_lf_<LF, NP, false>(P, s);
+}
+
+template <int LF, bool ILV>
+int launch_c4inv_x3_(const ColInvParams &P, cudaStream_t s)
+{
     static std::atomic<unsigned> mask{0};
-    const int smem = NP * C4<LF>::WORDS * 4;
-    FCIRC_TRY(c4_smem(k_colinv4<LF, NP>, smem, mask));
-    const uint64_t ncta = (uint64_t)1 << (P.l0 + (P.logn - P.l1) - 2 - C4<LF>::LNQ);
-    ProfScope ps("k_colinv4", s);
-    k_colinv4<LF, NP><<<(unsigned)ncta, kC4Threads, smem, s>>>(P);
+    const int smem = C4<LF>::WORDS * 4;
+    FCIRC_TRY(c4_smem(k_colinv4x3<LF, ILV>, smem, mask));
+    const uint64_t ncta = (uint64_t)3 << (P.l0 + (P.logn - P.l1) - 2 - C4<LF>::LNQ);
+    ProfScope ps("k_colinv4x3", s);
+    k_colinv4x3<LF, ILV><<<(unsigned)ncta, kC4Threads, smem, s>>>(P);
     FCIRC_CUDA_TRY(cudaGetLastError());
     return FCIRC_OK;
 }
@@ -816,14 +899,7 @@ int launch_c4inv_lf(const ColInvParams &P, cudaStream_t s)
 template <int LF>
 int launch_c4inv_x3(const ColInvParams &P, cudaStream_t s)
 {
-    static std::atomic<unsigned> mask{0};
-    const int smem = C4<LF>::WORDS * 4;
-    FCIRC_TRY(c4_smem(k_colinv4x3<LF>, smem, mask));
-    const uint64_t ncta = (uint64_t)3 << (P.l0 + (P.logn - P.l1) - 2 - C4<LF>::LNQ);
-    ProfScope ps("k_colinv4x3", s);
-    k_colinv4x3<LF><<<(unsigned)ncta, kC4Threads, smem, s>>>(P);
-    FCIRC_CUDA_TRY(cudaGetLastError());
-    return FCIRC_OK;
+    return P.ilv ? launch_c4inv_x3_<LF, true>(P, s) : launch_c4inv_x3_<LF, false>(P, s);
 }
 
 }  // namespace
@@ -855,6 +931,22 @@ bool col4_inv_ok(const ColInvParams &P)
     if (P.nprime != 1 && !(P.nprime == 3 && epi_crt(P.epi) && FCIRC_C4_X3)) return false;
     for (int q = 0; q < P.nprime; ++q)
         if (!aligned(P.job[q].src, 16) || (!epi_crt(P.epi) && !aligned(P.job[q].dst, 16))) return false;
+    return true;
+}
+
+bool col4_fwd_ilv_ok(const ColFwdParams &P, int nctay)
+{
+    if (!col4_fwd_ok(P, nctay) || P.logn - P.l1 != 12) return false;
+    for (int k = 0; k < nctay * P.jobs_per_cta; ++k)
+        if (!aligned(P.job[k].dst, 32)) return false;
+    return true;
+}
+
+bool col4_inv_ilv_ok(const ColInvParams &P)
+{
+    if (!col4_inv_ok(P) || P.logn - P.l1 != 12) return false;
+    for (int q = 0; q < P.nprime; ++q)
+        if (!aligned(P.job[q].src, 32)) return false;
     return true;
 }
 

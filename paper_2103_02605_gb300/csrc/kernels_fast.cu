@@ -403,6 +403,11 @@ static int launch_colfwd_lf(const ColFwdParams &P, int nctay, cudaStream_t s)
 
 int launch_colfwd(const ColFwdParams &P, int nctay, cudaStream_t s)
 {
+    // only the four-column kernels write the tile-pair interleaved layout
+    if (P.ilv) {
+        if (!col4_fwd_ilv_ok(P, nctay)) return fail(FCIRC_EINVAL, "column pass: interleaved output not possible here");
+        return launch_colfwd4(P, nctay, s);
+    }
 #if FCIRC_COL4
     if (col4_fwd_ok(P, nctay)) return launch_colfwd4(P, nctay, s);
 #endif
@@ -431,6 +436,11 @@ static int launch_colinv_lf(const ColInvParams &P, cudaStream_t s)
 
 int launch_colinv(const ColInvParams &P, cudaStream_t s)
 {
+    // only the four-column kernels read the tile-pair interleaved layout
+    if (P.ilv) {
+        if (!col4_inv_ilv_ok(P)) return fail(FCIRC_EINVAL, "column pass: interleaved input not possible here");
+        return launch_colinv4(P, s);
+    }
 #if FCIRC_COL4
     if (col4_inv_ok(P)) return launch_colinv4(P, s);
 #endif

@@ -46,11 +46,28 @@ struct TileJob {
 // needs no rotation of its output.
 enum : int { TILE_FULL = 0, TILE_ROW = 1, TILE_PLANNED = 2, TILE_SHIFT = 3 };
 
+// The tile-pair interleaved layout of the arrays between the column passes
+// and the 4096-residue tile kernel.  Seen by the column passes, such an array
+// is rows of 4096 residues, one row per tile.  Interleaved, rows 2t and
+// 2t + 1 share one 8192-word block in which every 32-byte sector holds one
+// column quad of both: residue i sits at ilv_pos(i), a permutation of bits
+// 2..12 of i (bit 12, the tile's parity, moves to bit 2).  A column pass
+// thread holding two adjacent rows of a quad then writes or reads whole
+// 32-byte sectors; a tile reads and writes only the positions of its own
+// residues, so it can work in place.
+__host__ __device__ __forceinline__ uint32_t ilv_pos(uint32_t i)
+{
+    return (i & ~0x1FFFu) | (((i >> 12) & 1u) << 2) | ((i & 0xFFCu) << 1) | (i & 3u);
+}
+
 struct TileParams {
     TileJob job[3];
     uint64_t N;
     int logT, D;
     int var = 0;           // TILE_FULL / ROW / PLANNED / SHIFT (tile_dev.cuh); logT = 12 only
+    // bit 0: the row-vector source, bit 1: the vector source and the
+    // destination, are in the tile-pair interleaved layout (logT = 12 only)
+    int ilv = 0;
 };
 
 struct StrFwdJob {
@@ -141,6 +158,7 @@ struct ColFwdParams {
     uint32_t N;
     int logn, l0, l1;
     int stage_off[3];
+    int ilv;               // write the tile-pair interleaved layout (ilv_pos); col4_fwd_ilv_ok
 };
 
 struct ColInvJob {
@@ -156,6 +174,7 @@ struct ColInvParams {
     uint32_t N;
     int logn, l0, l1;
     int stage_off[3];
+    int ilv;               // read the tile-pair interleaved layout (ilv_pos); col4_inv_ilv_ok
     int epi;
     uint64_t *dst64;
     uint64_t nout;
@@ -179,6 +198,11 @@ int launch_colinv(const ColInvParams &P, cudaStream_t s);
 // four columns per thread (kernels_col4.cu); used when these accept the pass
 bool col4_fwd_ok(const ColFwdParams &P, int nctay);
 bool col4_inv_ok(const ColInvParams &P);
+// whether the four-column kernels can write (forward) / read (inverse) the
+// tile-pair interleaved layout for this pass: the pass borders the tiles
+// (2^12 columns) and its arrays are 32-byte aligned
+bool col4_fwd_ilv_ok(const ColFwdParams &P, int nctay);
+bool col4_inv_ilv_ok(const ColInvParams &P);
 int launch_colfwd4(const ColFwdParams &P, int nctay, cudaStream_t s);
 int launch_colinv4(const ColInvParams &P, cudaStream_t s);
 // stage split of a column pass of lf levels: the first stage takes lf mod 4

@@ -30,7 +30,7 @@ __global__ void __launch_bounds__(256, FCIRC_TILE_MINB) k_tile4096(const __grid_
     const TileJob &J = P.job[blockIdx.y];
     const uint64_t t = blockIdx.x;
     tile4096_dev<MA, MX, VAR>(J, (uint32_t)P.N, (uint32_t)(t << 12), J.sig + t * (uint64_t)(11 * 6), SA, SX, STW,
-                              SITW);
+                              SITW, P.ilv);
 }
 
 bool fast_tile_ok(int logT) { return logT == 12; }

@@ -167,9 +167,12 @@ __device__ __forceinline__ int tphiC(int tC, int q) { return tC ^ (q << 2); }
 // tile's first index in arrays of length N; sg its 11 levels of factors
 // (6 words each, see plan.cu); SA, SX (4096 words each, 16-byte aligned),
 // STW, SITW (256 entries) are this CTA's shared memory.  256 threads.
+// ilv (TileParams::ilv): bit 0, the row vector is in the tile-pair
+// interleaved layout; bit 1, the vector and the destination are.  Residue
+// base + tid + 256 j then sits at ilv_pos(base + tid) + 512 j.
 template <int MA, int MX, int VAR = TILE_FULL>
 __device__ __forceinline__ void tile4096_dev(const TileJob &J, uint32_t N, uint32_t base, const uint32_t *sg,
-                                             uint32_t *SA, uint32_t *SX, Tw *STW, Tw *SITW)
+                                             uint32_t *SA, uint32_t *SX, Tw *STW, Tw *SITW, int ilv = 0)
 {
     constexpr bool DO_A = VAR != TILE_PLANNED, DO_X = VAR != TILE_ROW;
     const uint32_t p = J.p, p2 = 2 * J.p, pinv = J.pinv;
@@ -183,10 +186,13 @@ __device__ __forceinline__ void tile4096_dev(const TileJob &J, uint32_t N, uint3
         if (VAR != TILE_ROW) SITW[tid] = twiddle_from(J.Ui[tid], e[3], e[4], e[5], p);
     }
     uint32_t a[16], x[16];
+    const uint32_t ipos = ilv_pos(base + tid);
+    const uint32_t ia = (ilv & 1) ? ipos : base + tid, sa = (ilv & 1) ? 512u : 256u;
+    const uint32_t ix = (ilv & 2) ? ipos : base + tid, sx = (ilv & 2) ? 512u : 256u;
 #pragma unroll
     for (int j = 0; j < 16; ++j) {
-        if (DO_A) a[j] = ld_raw<MA>(J.a, N, base + tid + 256 * j);
-        if (DO_X) x[j] = ld_raw<MX>(J.x, N, base + tid + 256 * j);
+        if (DO_A) a[j] = ld_raw<MA>(J.a, N, ia + sa * j);
+        if (DO_X) x[j] = ld_raw<MX>(J.x, N, ix + sx * j);
     }
 #pragma unroll
     for (int j = 0; j < 16; ++j) {
@@ -332,7 +338,7 @@ __device__ __forceinline__ void tile4096_dev(const TileJob &J, uint32_t N, uint3
     for (int j = 0; j < 16; ++j) a[j] = SA[tphiA(tA, j)];
     rec1<4, 4>(a, [&](int d, int j) { return SITW[(1 << d) + j]; }, p, p2);
 #pragma unroll
-    for (int j = 0; j < 16; ++j) J.dst[base + tid + 256 * j] = J.store_lazy ? a[j] : reduce_once(a[j], p);
+    for (int j = 0; j < 16; ++j) J.dst[ix + sx * j] = J.store_lazy ? a[j] : reduce_once(a[j], p);
 }
 
 // Any tile size 2 <= T = 2^logT <= 4096 (D = logT - 1 halving levels), with

@@ -180,3 +180,43 @@ def test_four_column_address_identities(LF):
                         kt = ((row0 >> 4) & 7) ^ qs(quad)
                         got = (quad << (LF + 2)) + (row0 << 2) + ((i ^ kt) << 2)
                     assert got == want
+
+
+def _ilv_pos(i):
+    """Python restatement of ilv_pos (kernels_mod.hpp): bits 2..12 of i
+    rotated so that bit 12 (the tile's parity) becomes bit 2."""
+    return (i & ~0x1FFF) | (((i >> 12) & 1) << 2) | ((i & 0xFFC) << 1) | (i & 3)
+
+
+def test_tile_pair_interleave_is_a_permutation_of_each_pair_block():
+    import numpy as np
+    i = np.arange(1 << 16, dtype=np.int64)
+    p = _ilv_pos(i)
+    assert np.array_equal(np.sort(p), i)                   # a permutation
+    assert np.array_equal(p >> 13, i >> 13)                # inside its 8192-word block
+    # a column quad of rows 2t and 2t + 1 fills one aligned 32-byte sector
+    for t in (0, 2, 6, 14):
+        for q in (0, 1, 511, 1023):
+            words = [_ilv_pos((t + r) * 4096 + 4 * q + c) for r in (0, 1) for c in range(4)]
+            assert words == list(range(words[0], words[0] + 8)) and words[0] % 8 == 0
+
+
+def test_interleave_address_identities_of_the_kernels():
+    """The closed forms the kernels use instead of ilv_pos per element: the
+    tile kernel's residue base + tid + 256 j at ilv_pos(base + tid) + 512 j,
+    and the column passes' row pair k of rows row0.. (row0 a multiple of 16)
+    at ilv_pos(origin) + 8192 k."""
+    for base in (0, 4096, 8192, 3 * 4096, 4095 * 4096):
+        for tid in range(256):
+            b = _ilv_pos(base + tid)
+            for j in range(16):
+                assert _ilv_pos(base + tid + 256 * j) == b + 512 * j
+    for pb_base in (0, 1 << 24):
+        for quad in (0, 1, 7, 1023):
+            for row0 in range(0, 4096, 16):
+                o = pb_base + 4 * quad + (row0 << 12)
+                for k in range(8):
+                    for c in range(4):
+                        assert _ilv_pos(o + ((row0 + 2 * k) << 12) - (row0 << 12) + c) == _ilv_pos(o) + 8192 * k + c
+                        assert _ilv_pos(o + ((row0 + 2 * k + 1) << 12) - (row0 << 12) + c) == \
+                            _ilv_pos(o) + 8192 * k + 4 + c
