@@ -430,6 +430,19 @@ int fcirc_set_checks(int on);
  */
 int fcirc_debug_fail_alloc(int k);
 
+/*
+ * fcirc_debug_spin_limit -- the bound of the library's device-side waits:
+ * the tile kernel's thread 0 probes the mbarrier its TMA loads complete on
+ * at most `probes` times (mbarrier.try_wait, each probe itself time
+ * limited).  A CTA whose wait gives up records FCIRC_ETIMEOUT in the sticky
+ * device status word (fcirc_sync_status returns it), waits for the copies it
+ * started, and leaves its tile unfinished; the call's result is then
+ * unspecified but nothing faults.  probes = 0 makes every such wait give up
+ * at once (for tests); probes < 0 restores the default (2^22).  Applies to
+ * calls made afterwards.  Always FCIRC_OK.
+ */
+int fcirc_debug_spin_limit(long long probes);
+
 #ifdef __cplusplus
 }
 #endif

@@ -72,6 +72,7 @@ _SIGNATURES = {
     "fcirc_release": ([], _i32),
     "fcirc_set_checks": ([_i32], _i32),
     "fcirc_debug_fail_alloc": ([_i32], _i32),
+    "fcirc_debug_spin_limit": ([ctypes.c_longlong], _i32),
     "fcirc_nth_root": ([_u32, _u32, _u32, ctypes.POINTER(_u32)], _i32),
     "fcirc_gf_nth_root": ([_u32, _u32, _u32, ctypes.POINTER(_u32), ctypes.POINTER(_u32)], _i32),
     "fcirc_node_twiddle": ([_u32, _u32, _u64, _u32, _u64, ctypes.POINTER(_u32), ctypes.POINTER(_u32)], _i32),

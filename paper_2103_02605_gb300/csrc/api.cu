@@ -337,6 +337,7 @@ static int matvec_core(const Plan *pl, const Src &sa, const Src &sx, uint32_t *d
         tp.logT = pl->logT;
         tp.D = pl->D;
         tp.ilv = ilv ? 3 : 0;
+        FCIRC_TRY(tile_tma_maps(tp, 1));
         FCIRC_TRY(run_tile(tp, (uint64_t)1 << pl->k, 1, s));
     }
     for (int i = last; i >= 0; --i) {
@@ -454,6 +455,7 @@ static int poly_core(const uint16_t *P, uint64_t np, const uint16_t *Q, uint64_t
         tp.D = p0.D;
         tp.var = shift ? TILE_SHIFT : TILE_FULL;
         tp.ilv = ilv ? 3 : 0;
+        FCIRC_TRY(tile_tma_maps(tp, 3));
         FCIRC_TRY(run_tile(tp, (uint64_t)1 << p0.k, 3, s));
     }
     for (int i = last; i >= 0; --i)
@@ -701,6 +703,7 @@ int fcirc_matvec_aplan(fcirc_aplan_t h, const uint32_t *x, uint32_t *c, void *st
         tp.D = pl->D;
         tp.var = TILE_PLANNED;
         tp.ilv = ilv ? 2 : 0;
+        FCIRC_TRY(tile_tma_maps(tp, 1));
         FCIRC_TRY(run_tile(tp, (uint64_t)1 << pl->k, 1, s));
     }
     for (int i = last; i >= 0; --i) {

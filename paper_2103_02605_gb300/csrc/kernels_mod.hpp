@@ -1,5 +1,6 @@
 // kernels_mod.hpp -- parameter blocks and launchers of the modular kernels.
 #pragma once
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -68,7 +69,20 @@ struct TileParams {
     // bit 0: the row-vector source, bit 1: the vector source and the
     // destination, are in the tile-pair interleaved layout (logT = 12 only)
     int ilv = 0;
+    // With tma = 1 the interleaved sides and the destination move through
+    // TMA tensor copies (tmap[job][0]: row vector, [1]: vector, [2]:
+    // destination, tile_tma_maps); the loads' mbarrier wait gives up after
+    // spin_limit probes and then reports FCIRC_ETIMEOUT in *status.
+    int tma = 0;
+    uint32_t spin_limit = 0;
+    uint32_t *status = nullptr;
+    CUtensorMap tmap[3][3];
 };
+
+// Fills P.tmap for the interleaved arrays of P's first njobs jobs and sets
+// P.tma, P.spin_limit and P.status; leaves P.tma = 0 (scalar accesses) when
+// the driver offers no tensor-map encoder.  tma_host.cu.
+int tile_tma_maps(TileParams &P, int njobs);
 
 struct StrFwdJob {
     Src src;

@@ -20,17 +20,19 @@ namespace fcirc {
 #define FCIRC_TILE_MINB 3
 #endif
 
-template <int MA, int MX, int VAR = TILE_FULL>
+template <int MA, int MX, int VAR = TILE_FULL, bool TMA = false>
 __global__ void __launch_bounds__(256, FCIRC_TILE_MINB) k_tile4096(const __grid_constant__ TileParams P)
 {
-    __shared__ __align__(16) uint32_t SA[4096];
-    __shared__ __align__(16) uint32_t SX[4096];
+    __shared__ __align__(128) uint32_t SA[4096];
+    __shared__ __align__(128) uint32_t SX[4096];
     __shared__ Tw STW[256];
     __shared__ Tw SITW[256];
+    __shared__ uint64_t bar;
+    __shared__ uint32_t flag;
     const TileJob &J = P.job[blockIdx.y];
     const uint64_t t = blockIdx.x;
-    tile4096_dev<MA, MX, VAR>(J, (uint32_t)P.N, (uint32_t)(t << 12), J.sig + t * (uint64_t)(11 * 6), SA, SX, STW,
-                              SITW, P.ilv);
+    tile4096_dev<MA, MX, VAR, TMA>(J, (uint32_t)P.N, (uint32_t)(t << 12), J.sig + t * (uint64_t)(11 * 6), SA, SX,
+                                   STW, SITW, P.ilv, &P, (int)blockIdx.y, &bar, &flag);
 }
 
 bool fast_tile_ok(int logT) { return logT == 12; }
@@ -52,6 +54,26 @@ int launch_tile_fast(const TileParams &P, uint64_t ntiles, int njobs, cudaStream
             k_tile4096<MODE_U32_S, MODE_U32, TILE_ROW><<<grid, 256, 0, s>>>(P);
         else
             return fail(FCIRC_EINVAL, "tile kernel: unsupported row source mode %d", ma);
+        FCIRC_CUDA_TRY(cudaGetLastError());
+        return FCIRC_OK;
+    }
+    if (P.tma) {
+        // interleaved sides through TMA: plain scratch sources only
+        if (ma != MODE_U32 || mx != MODE_U32 || !P.ilv)
+            return fail(FCIRC_EINVAL, "tile kernel: TMA copies need interleaved plain sources (%d/%d)", ma, mx);
+        if (P.var == TILE_PLANNED)
+            for (int k = 0; k < njobs; ++k)
+                if ((reinterpret_cast<uintptr_t>(P.job[k].a.ptr) & 15) != 0)
+                    return fail(FCIRC_EINVAL, "tile kernel: unaligned transformed row vector");
+        ProfScope ps(P.var == TILE_PLANNED ? "k_tile4096_planned" : "k_tile4096", s);
+        if (P.var == TILE_SHIFT)
+            k_tile4096<MODE_U32, MODE_U32, TILE_SHIFT, true><<<grid, 256, 0, s>>>(P);
+        else if (P.var == TILE_PLANNED)
+            k_tile4096<MODE_U32, MODE_U32, TILE_PLANNED, true><<<grid, 256, 0, s>>>(P);
+        else if (P.var == TILE_FULL)
+            k_tile4096<MODE_U32, MODE_U32, TILE_FULL, true><<<grid, 256, 0, s>>>(P);
+        else
+            return fail(FCIRC_EINVAL, "tile kernel: no TMA form of variant %d", P.var);
         FCIRC_CUDA_TRY(cudaGetLastError());
         return FCIRC_OK;
     }

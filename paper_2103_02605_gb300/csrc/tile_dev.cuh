@@ -8,6 +8,7 @@
 
 #include "kernels_mod.hpp"
 #include "modarith.cuh"
+#include "tma.cuh"
 
 namespace fcirc {
 
@@ -170,13 +171,40 @@ __device__ __forceinline__ int tphiC(int tC, int q) { return tC ^ (q << 2); }
 // ilv (TileParams::ilv): bit 0, the row vector is in the tile-pair
 // interleaved layout; bit 1, the vector and the destination are.  Residue
 // base + tid + 256 j then sits at ilv_pos(base + tid) + 512 j.
-template <int MA, int MX, int VAR = TILE_FULL>
+//
+// TMA: the interleaved sides arrive as TMA tensor copies (TP->tmap of job jq:
+// four boxes of 256 column quads per side) in natural order in SA / SX, and
+// the products leave the same way from SX.  Thread 0 issues the copies and
+// waits on the mbarrier *bar with at most TP->spin_limit probes; if it gives
+// up, it records FCIRC_ETIMEOUT in *TP->status, waits (bounded) for the
+// copies still in flight, and the whole CTA returns.  SA, SX 128-byte
+// aligned; *flag a shared word.
+constexpr uint32_t kTmaDrainProbes = 1u << 24;
+
+template <int MA, int MX, int VAR = TILE_FULL, bool TMA = false>
 __device__ __forceinline__ void tile4096_dev(const TileJob &J, uint32_t N, uint32_t base, const uint32_t *sg,
-                                             uint32_t *SA, uint32_t *SX, Tw *STW, Tw *SITW, int ilv = 0)
+                                             uint32_t *SA, uint32_t *SX, Tw *STW, Tw *SITW, int ilv = 0,
+                                             const TileParams *TP = nullptr, int jq = 0, uint64_t *bar = nullptr,
+                                             uint32_t *flag = nullptr)
 {
     constexpr bool DO_A = VAR != TILE_PLANNED, DO_X = VAR != TILE_ROW;
     const uint32_t p = J.p, p2 = 2 * J.p, pinv = J.pinv;
     const int tid = threadIdx.x;
+    // the TMA form: the vector and the destination always through TMA, the
+    // row vector too unless it is a plan's transformed one (tile_tma_maps)
+    constexpr bool tma_a = TMA && DO_A && VAR != TILE_PLANNED, tma_x = TMA && DO_X;
+    const int tp = (int)(base >> 12);   // tile index: pair tp >> 1, parity tp & 1
+    if constexpr (TMA) {
+        if (tid == 0) {
+            mbar_init(bar, 1);
+            mbar_arrive_expect_tx(bar, (tma_a ? 16384u : 0u) + (tma_x ? 16384u : 0u));
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                if (tma_a) tma_load_4d(SA + 1024 * i, &TP->tmap[jq][0], bar, 0, tp & 1, 256 * i, tp >> 1);
+                if (tma_x) tma_load_4d(SX + 1024 * i, &TP->tmap[jq][1], bar, 0, tp & 1, 256 * i, tp >> 1);
+            }
+        }
+    }
 
     // twiddles of tile levels 0..7 (heap index 1..255), one per thread
     if (tid > 0) {
@@ -189,10 +217,26 @@ __device__ __forceinline__ void tile4096_dev(const TileJob &J, uint32_t N, uint3
     const uint32_t ipos = ilv_pos(base + tid);
     const uint32_t ia = (ilv & 1) ? ipos : base + tid, sa = (ilv & 1) ? 512u : 256u;
     const uint32_t ix = (ilv & 2) ? ipos : base + tid, sx = (ilv & 2) ? 512u : 256u;
+    if constexpr (TMA) {
+        if (tid == 0) {
+            const bool ok = mbar_wait_bounded(bar, 0, TP->spin_limit);
+            if (!ok) {
+                atomicCAS(TP->status, 0u, (uint32_t)FCIRC_ETIMEOUT);
+                // the copies still in flight land in this CTA's shared memory
+                mbar_wait_bounded(bar, 0, kTmaDrainProbes);
+            }
+            *flag = ok ? 1u : 0u;
+        }
+        __syncthreads();
+        if (*flag == 0) return;   // the same verdict for every thread
+        // the phase has completed: each thread's own probe succeeds at once
+        // and makes the copied data visible to it
+        mbar_wait_bounded(bar, 0, kTmaDrainProbes);
+    }
 #pragma unroll
     for (int j = 0; j < 16; ++j) {
-        if (DO_A) a[j] = ld_raw<MA>(J.a, N, ia + sa * j);
-        if (DO_X) x[j] = ld_raw<MX>(J.x, N, ix + sx * j);
+        if (DO_A) a[j] = tma_a ? SA[tid + 256 * j] : ld_raw<MA>(J.a, N, ia + sa * j);
+        if (DO_X) x[j] = tma_x ? SX[tid + 256 * j] : ld_raw<MX>(J.x, N, ix + sx * j);
     }
 #pragma unroll
     for (int j = 0; j < 16; ++j) {
@@ -337,6 +381,20 @@ __device__ __forceinline__ void tile4096_dev(const TileJob &J, uint32_t N, uint3
 #pragma unroll
     for (int j = 0; j < 16; ++j) a[j] = SA[tphiA(tA, j)];
     rec1<4, 4>(a, [&](int d, int j) { return SITW[(1 << d) + j]; }, p, p2);
+    if constexpr (TMA) {
+        // the products through SX (free since the leaves) and four TMA boxes
+#pragma unroll
+        for (int j = 0; j < 16; ++j) SX[tid + 256 * j] = J.store_lazy ? a[j] : reduce_once(a[j], p);
+        fence_async_shared();
+        __syncthreads();
+        if (tid == 0) {
+#pragma unroll
+            for (int i = 0; i < 4; ++i) tma_store_4d(&TP->tmap[jq][2], SX + 1024 * i, 0, tp & 1, 256 * i, tp >> 1);
+            tma_store_commit();
+            tma_store_wait_read();   // SX stays valid until the stores have read it
+        }
+        return;
+    }
 #pragma unroll
     for (int j = 0; j < 16; ++j) J.dst[ix + sx * j] = J.store_lazy ? a[j] : reduce_once(a[j], p);
 }

@@ -133,3 +133,32 @@ def test_status_word_allocation_failure():
     r = subprocess.run([sys.executable, "-c", code], cwd=root, capture_output=True, text=True, timeout=600)
     assert r.returncode == 0, r.stderr[-2000:]
     assert r.stdout.split()[-2:] == ["3", "0"], r.stdout
+
+
+@pytest.mark.parametrize("m", [20, 24])
+def test_bounded_tma_wait_reports_a_timeout(F, orc, m):
+    """The tile kernel's TMA loads complete on an mbarrier that thread 0
+    probes a bounded number of times.  With the bound at zero probes every
+    wait gives up at once: the call still completes (each CTA waits for its
+    own copies, then leaves its tile), fcirc_sync_status returns
+    FCIRC_ETIMEOUT once, and with the default bound the next call is exact."""
+    import torch
+    L = F.load()
+    n = 1 << m
+    a, x = I.single_mod(n, P1, seed=45)
+    rows = np.array([0, 1, 4097, n // 2 + 3, n - 1], np.uint64)
+    want = orc.fcirc_matvec_mod_rows(P1, 1, a, x, rows)
+    da, dx = dev(a), dev(x)
+    assert F.sync_status() == 0
+    L.fcirc_debug_spin_limit(0)
+    try:
+        F.fcirc_matvec(P1, 1, da, dx)
+        torch.cuda.synchronize()
+        assert F.sync_status() == 5          # FCIRC_ETIMEOUT, then cleared
+        assert F.sync_status() == 0
+    finally:
+        L.fcirc_debug_spin_limit(-1)
+    c = F.fcirc_matvec(P1, 1, da, dx)
+    torch.cuda.synchronize()
+    assert np.array_equal(c.cpu().numpy().view(np.uint32)[rows.astype(np.int64)], want)
+    assert F.sync_status() == 0
