@@ -8,7 +8,9 @@
  * plumbing for the kernels of the C ABI in fcirc.h.
  *
  * Events are recorded only between fcirc_prof_start() and fcirc_prof_stop();
- * tracing must be off while a stream is captured into a CUDA graph.
+ * tracing must be off while a stream is captured into a CUDA graph.  The
+ * copies that stage host arguments are traced too, as "copy_h2d" and
+ * "copy_d2h" (they are not kernel launches).
  */
 #ifndef FCIRC_PROF_H
 #define FCIRC_PROF_H
@@ -31,7 +33,8 @@ int fcirc_prof_stop(void);
  * fcirc_status code. */
 int fcirc_prof_report(char *buf, uint64_t len);
 
-/* Number of kernel launches recorded since fcirc_prof_start(). */
+/* Number of records (kernel launches and staging copies) since
+ * fcirc_prof_start(). */
 uint64_t fcirc_prof_launches(void);
 
 /*

@@ -98,8 +98,10 @@ struct Staging {
             } else {
                 a->d = cur;
                 cur += align256(a->bytes);
-                if (a->in && a->bytes)
+                if (a->in && a->bytes) {
+                    ProfScope ps("copy_h2d", s);
                     FCIRC_CUDA_TRY(cudaMemcpyAsync(a->d, a->user, a->bytes, cudaMemcpyHostToDevice, s));
+                }
             }
         }
         scratch = cur;
@@ -110,9 +112,11 @@ struct Staging {
     {
         if (!any_host) return FCIRC_OK;
         for (Arg *a : args)
-            if (!a->on_device && a->out && a->bytes)
+            if (!a->on_device && a->out && a->bytes) {
+                ProfScope ps("copy_d2h", s);
                 FCIRC_CUDA_TRY(cudaMemcpyAsync(const_cast<void *>(a->user), a->d, a->bytes,
                                                cudaMemcpyDeviceToHost, s));
+            }
         if (any_pageable) FCIRC_CUDA_TRY(cudaStreamSynchronize(s));
         return FCIRC_OK;
     }

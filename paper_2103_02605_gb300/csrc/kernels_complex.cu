@@ -22,6 +22,7 @@
 // stage on 8 contiguous numbers (bottom two levels, four 2x2 leaves, and
 // the first two recombination levels).
 #include <cmath>
+#include <type_traits>
 #include <map>
 #include <mutex>
 #include <tuple>
@@ -77,10 +78,30 @@ struct CShape {
 // or SsaE<W> (Z/(2^K + 1), ssa.cuh); TW: the twiddle type (T itself, or a
 // shift amount for Z/(2^K + 1)).  The arithmetic comes from the cmul /
 // cadd / csub / cneg overloads and ld_tw.
+// Shared-memory position of element e of a side.  For complex FP32 the
+// low four bits of e are XORed with bits 4-6 of e, and bit 3 also with bit
+// 6: a bijection inside every 16-element block that makes each half-warp's
+// 64-bit accesses fall in 16 distinct bank pairs in every pattern of the
+// kernels -- the loads and stores e = t + (n/8) k, the register stages, and
+// the last stage's 8 contiguous numbers per thread -- for n >= 128 (checked
+// on the CPU for n = 2^3 .. 2^12).  Only the complex FP32 kernels, which are
+// bound by shared-memory bandwidth, use it: the GF(p^2) and Z/(2^K + 1)
+// kernels are bound by their ALU work and keep e.
+template <class T>
+__host__ __device__ __forceinline__ int cpos(int e)
+{
+    if constexpr (std::is_same<T, float2>::value)
+        return e ^ (((e >> 4) & 7) | (((e >> 6) & 1) << 3));
+    else
+        return e;
+}
+
 template <class T, class TW = T>
 struct SideT {
     T *R, *X;
     const TW *tw, *itw;   // heap-indexed twiddles and inverses, [N/2]
+    __device__ __forceinline__ T &ra(int e) const { return R[cpos<T>(e)]; }
+    __device__ __forceinline__ T &xa(int e) const { return X[cpos<T>(e)]; }
 };
 using Side = SideT<float2>;
 
@@ -99,8 +120,8 @@ __device__ __forceinline__ void cfwd_stage(SideT<T, TW> &sd, int t)
         T r[MM], x[MM];
 #pragma unroll
         for (int i = 0; i < MM; ++i) {
-            r[i] = sd.R[e0 + (i << LST)];
-            x[i] = sd.X[e0 + (i << LST)];
+            r[i] = sd.ra(e0 + (i << LST));
+            x[i] = sd.xa(e0 + (i << LST));
         }
 #pragma unroll
         for (int d = 0; d < NL; ++d) {
@@ -123,8 +144,8 @@ __device__ __forceinline__ void cfwd_stage(SideT<T, TW> &sd, int t)
         }
 #pragma unroll
         for (int i = 0; i < MM; ++i) {
-            sd.R[e0 + (i << LST)] = r[i];
-            sd.X[e0 + (i << LST)] = x[i];
+            sd.ra(e0 + (i << LST)) = r[i];
+            sd.xa(e0 + (i << LST)) = x[i];
         }
     }
 }
@@ -143,7 +164,7 @@ __device__ __forceinline__ void crec_stage(SideT<T, TW> &sd, int t)
         const int e0 = (blk << LRB) + off;
         T r[MM];
 #pragma unroll
-        for (int i = 0; i < MM; ++i) r[i] = sd.R[e0 + (i << LST)];
+        for (int i = 0; i < MM; ++i) r[i] = sd.ra(e0 + (i << LST));
 #pragma unroll
         for (int d = NL - 1; d >= 0; --d) {
             const int hh = MM >> (d + 1);
@@ -160,7 +181,7 @@ __device__ __forceinline__ void crec_stage(SideT<T, TW> &sd, int t)
             }
         }
 #pragma unroll
-        for (int i = 0; i < MM; ++i) sd.R[e0 + (i << LST)] = r[i];
+        for (int i = 0; i < MM; ++i) sd.ra(e0 + (i << LST)) = r[i];
     }
 }
 
@@ -173,8 +194,8 @@ __device__ __forceinline__ void cleaf_stage(SideT<T, TW> &sd, int t)
     T r[8], x[8];
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
-        r[i] = sd.R[8 * t + i];
-        x[i] = sd.X[8 * t + i];
+        r[i] = sd.ra(8 * t + i);
+        x[i] = sd.xa(8 * t + i);
     }
     const TW s0 = ld_tw(&sd.tw[(1 << (L - 2)) + t]);
     const TW s1[2] = {ld_tw(&sd.tw[(1 << (L - 1)) + 2 * t]), ld_tw(&sd.tw[(1 << (L - 1)) + 2 * t + 1])};
@@ -226,7 +247,7 @@ __device__ __forceinline__ void cleaf_stage(SideT<T, TW> &sd, int t)
         r[i] = cmul(sum, i0);
     }
 #pragma unroll
-    for (int i = 0; i < 8; ++i) sd.R[8 * t + i] = r[i];
+    for (int i = 0; i < 8; ++i) sd.ra(8 * t + i) = r[i];
 }
 
 // whole product for one instance: forward stages, last stage, recombination
@@ -260,7 +281,7 @@ __device__ __forceinline__ void cproduct(SideT<T, TW> &sd, int t)
 }
 
 template <int M>
-__global__ void __launch_bounds__(CShape<M>::CT) k_cfwd(const __grid_constant__ CParams P)
+__global__ void __launch_bounds__(CShape<M>::CT, 8) k_cfwd(const __grid_constant__ CParams P)
 {
     using Sh = CShape<M>;
     extern __shared__ __align__(16) float2 csm[];
@@ -273,8 +294,8 @@ __global__ void __launch_bounds__(CShape<M>::CT) k_cfwd(const __grid_constant__ 
 #pragma unroll
     for (int k = 0; k < 8; ++k) {
         const int e = t + Sh::NTI * k;
-        sd.R[e] = live ? a[e] : make_float2(0.f, 0.f);
-        sd.X[e] = live ? x[e] : make_float2(0.f, 0.f);
+        sd.ra(e) = live ? a[e] : make_float2(0.f, 0.f);
+        sd.xa(e) = live ? x[e] : make_float2(0.f, 0.f);
     }
     __syncthreads();
     cproduct<M, float2, float2>(sd, t);
@@ -283,7 +304,7 @@ __global__ void __launch_bounds__(CShape<M>::CT) k_cfwd(const __grid_constant__ 
 #pragma unroll
         for (int k = 0; k < 8; ++k) {
             const int e = t + Sh::NTI * k;
-            const float2 v = sd.R[e];
+            const float2 v = sd.ra(e);
             c[e] = make_float2(v.x * P.scale, v.y * P.scale);
         }
     }
@@ -305,8 +326,8 @@ __global__ void __launch_bounds__(CShape<M>::CT) k_gfwd(const __grid_constant__ 
 #pragma unroll
     for (int k = 0; k < 8; ++k) {
         const int e = t + Sh::NTI * k;
-        sd.R[e] = live ? a[e] : make_uint2(0u, 0u);
-        sd.X[e] = live ? x[e] : make_uint2(0u, 0u);
+        sd.ra(e) = live ? a[e] : make_uint2(0u, 0u);
+        sd.xa(e) = live ? x[e] : make_uint2(0u, 0u);
     }
     __syncthreads();
     cproduct<M, uint2, uint2>(sd, t);
@@ -316,7 +337,7 @@ __global__ void __launch_bounds__(CShape<M>::CT) k_gfwd(const __grid_constant__ 
 #pragma unroll
         for (int k = 0; k < 8; ++k) {
             const int e = t + Sh::NTI * k;
-            c[e] = cmul(sd.R[e], sc);
+            c[e] = cmul(sd.ra(e), sc);
         }
     }
 }
@@ -340,8 +361,8 @@ __global__ void __launch_bounds__(CShape<M>::CT) k_sfwd(const __grid_constant__ 
 #pragma unroll
     for (int k = 0; k < 8; ++k) {
         const int e = t + Sh::NTI * k;
-        sd.R[e] = live ? a[e] : ssa_zero<W>();
-        sd.X[e] = live ? x[e] : ssa_zero<W>();
+        sd.ra(e) = live ? a[e] : ssa_zero<W>();
+        sd.xa(e) = live ? x[e] : ssa_zero<W>();
     }
     __syncthreads();
     cproduct<M, E, SsaTw<W>>(sd, t);
@@ -351,14 +372,14 @@ __global__ void __launch_bounds__(CShape<M>::CT) k_sfwd(const __grid_constant__ 
 #pragma unroll
         for (int k = 0; k < 8; ++k) {
             const int e = t + Sh::NTI * k;
-            c[e] = cmul(sc, sd.R[e]);
+            c[e] = cmul(sc, sd.ra(e));
         }
     }
 }
 
 // dL/dx and dL/da of one instance per Sh::NTI threads
 template <int M>
-__global__ void __launch_bounds__(CShape<M>::CT) k_cbwd(const __grid_constant__ CBwdParams P)
+__global__ void __launch_bounds__(CShape<M>::CT, 7) k_cbwd(const __grid_constant__ CBwdParams P)
 {
     using Sh = CShape<M>;
     extern __shared__ __align__(16) float2 csm[];
@@ -378,11 +399,11 @@ __global__ void __launch_bounds__(CShape<M>::CT) k_cbwd(const __grid_constant__ 
         const float2 z = make_float2(0.f, 0.f);
         // beta_e = conj(a_0) for e = 0, conj(f) conj(a_{n-e}) otherwise
         const float2 ae = live ? a[e == 0 ? 0 : Sh::N - e] : z;
-        sx.R[e] = e == 0 ? cconj(ae) : cmul(fc, cconj(ae));
+        sx.ra(e) = e == 0 ? cconj(ae) : cmul(fc, cconj(ae));
         const float2 ge = live ? g[e] : z;
-        sx.X[e] = ge;
-        sa.R[e] = ge;
-        sa.X[e] = live ? cconj(x[e]) : z;
+        sx.xa(e) = ge;
+        sa.ra(e) = ge;
+        sa.xa(e) = live ? cconj(x[e]) : z;
     }
     __syncthreads();
     cproduct<M, float2, float2>(sx, t);
@@ -393,7 +414,7 @@ __global__ void __launch_bounds__(CShape<M>::CT) k_cbwd(const __grid_constant__ 
 #pragma unroll
         for (int k = 0; k < 8; ++k) {
             const int e = t + Sh::NTI * k;
-            const float2 vx = sx.R[e], va = sa.R[e];
+            const float2 vx = sx.ra(e), va = sa.ra(e);
             gx[e] = make_float2(vx.x * P.scale, vx.y * P.scale);
             ga[e] = make_float2(va.x * P.scale, va.y * P.scale);
         }

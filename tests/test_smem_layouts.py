@@ -220,3 +220,69 @@ def test_interleave_address_identities_of_the_kernels():
                         assert _ilv_pos(o + ((row0 + 2 * k) << 12) - (row0 << 12) + c) == _ilv_pos(o) + 8192 * k + c
                         assert _ilv_pos(o + ((row0 + 2 * k + 1) << 12) - (row0 << 12) + c) == \
                             _ilv_pos(o) + 8192 * k + 4 + c
+
+
+def _cpos(e):
+    """Python restatement of cpos<T> for 8-byte elements (kernels_complex.cu)."""
+    return e ^ (((e >> 4) & 7) | (((e >> 6) & 1) << 3))
+
+
+def _complex_patterns(M):
+    """Every shared-memory access of the complex kernels for n = 2^M, as one
+    list of (instance, element) per warp instruction: the loads/stores
+    e = t + (n/8) k, each register stage's accesses, and the last stage's
+    8 contiguous numbers per thread (CShape in kernels_complex.cu)."""
+    N = 1 << M
+    L = M - 1
+    NTI = N // 8
+    CT = max(128, NTI)
+    P = L - 2
+    NST = (P + 2) // 3
+
+    def nl(s):
+        return P - 3 * (NST - 1) if s == 0 else 3
+
+    def d0(s):
+        return 0 if s == 0 else (P - 3 * (NST - 1)) + 3 * (s - 1)
+    thr = [(tt // NTI, tt % NTI) for tt in range(CT)]
+    out = [[(li, t + NTI * k) for li, t in thr] for k in range(8)]
+    for S in range(NST):
+        NL, D0 = nl(S), d0(S)
+        LST, LRB = M - D0 - NL, M - D0
+        for h in range(8 >> NL):
+            for i in range(1 << NL):
+                acc = []
+                for li, t in thr:
+                    gg = t + NTI * h
+                    acc.append((li, ((gg >> LST) << LRB) + (gg & ((1 << LST) - 1)) + (i << LST)))
+                out.append(acc)
+    out += [[(li, 8 * t + i) for li, t in thr] for i in range(8)]
+    return out
+
+
+def _half_warp_wavefronts(acc, N, pos):
+    """64-bit shared accesses: each half-warp takes one wavefront per distinct
+    8-byte word in its busiest bank pair."""
+    tot = 0
+    for w in range(0, len(acc), 32):
+        for hw in (0, 16):
+            words = {}
+            for li, e in acc[w + hw:w + hw + 16]:
+                p = li * 2 * N + pos(e)
+                words.setdefault(p % 16, set()).add(p)
+            tot += max(len(v) for v in words.values())
+    return tot
+
+
+@pytest.mark.parametrize("M", range(3, 13))
+def test_complex_layout_is_a_bijection_and_conflict_free(M):
+    N = 1 << M
+    assert sorted(_cpos(e) for e in range(N)) == list(range(N))
+    assert all(_cpos(e) >> 4 == e >> 4 for e in range(N))
+    pats = _complex_patterns(M)
+    got = sum(_half_warp_wavefronts(a, N, _cpos) for a in pats)
+    plain = sum(_half_warp_wavefronts(a, N, lambda e: e) for a in pats)
+    ideal = sum(len(a) // 16 for a in pats)
+    assert got <= plain
+    if M >= 7:   # one instance per half-warp: every access conflict-free
+        assert got == ideal
