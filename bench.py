@@ -281,12 +281,12 @@ def kernel_bytes():
 _KSRC = {
     "k_colfwd4": ["kernels_col4.cu", "cluster.cuh", "tile_dev.cuh", "modarith.cuh", "kernels_mod.hpp"],
     "k_colinv4x3": ["kernels_col4.cu", "cluster.cuh", "tile_dev.cuh", "modarith.cuh", "kernels_mod.hpp"],
-    "k_tile4096": ["kernels_tile.cu", "tile_dev.cuh", "modarith.cuh", "kernels_mod.hpp"],
+    "k_tile4096": ["kernels_tile.cu", "tile_dev.cuh", "tma.cuh", "modarith.cuh", "kernels_mod.hpp"],
 }
 NCU_TRAFFIC = {
-    "k_colfwd4": (381068800, "0b6340b27c0e0bb3"),
-    "k_tile4096": (563151104, "33925eae45968c44"),
-    "k_colinv4x3": (304178944, "0b6340b27c0e0bb3"),
+    "k_colfwd4": (382039552, "28a3198ab4dfa901"),
+    "k_tile4096": (564267520, "1c365d591b51413b"),
+    "k_colinv4x3": (304484864, "28a3198ab4dfa901"),
 }
 
 
