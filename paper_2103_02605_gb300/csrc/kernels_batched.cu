@@ -118,57 +118,103 @@ __device__ __forceinline__ Tw tw_of(uint32_t w, uint32_t p) { return Tw{w, host:
 // The top K levels of an instance of n = 2^m residues viewed as 2^K rows of
 // C = n / 2^K columns: forward on both sides (row vector into c, vector into
 // xs) with twiddles FT (heap order), or recombination of c with FIT.
+// Several columns per iteration, both sides' loads issued before any
+// arithmetic: up to 32 residues in flight per thread (16 when the columns
+// are short), so that one DRAM latency serves both sides or several columns
+// (CPI columns of 2^K rows each).  C, a
+// power of two >= 2048, is a multiple of 256 CPI.
+template <int K>
+struct ColsShape {
+    static constexpr int R = 1 << K;
+    static constexpr bool BOTH = 2 * R <= 32;                     // both sides' loads together
+    static constexpr int CPI = 2 * R <= 16 ? 16 / (2 * R) : 1;
+    static constexpr int CPI_REC = R <= 16 ? 16 / R : 1;
+};
+
 template <int K>
 __device__ void cols_fwd(const BatchParams &P, uint64_t off, uint32_t C, const Tw *FT, Tw kt)
 {
+    using Sh = ColsShape<K>;
+    constexpr int R = Sh::R, CPI = Sh::CPI;
     const uint32_t p = P.p, p2 = 2 * P.p;
-    for (uint32_t col = threadIdx.x; col < C; col += kBThreads) {
-        uint32_t v[1 << K];
+    for (uint32_t col0 = threadIdx.x; col0 < C; col0 += kBThreads * CPI) {
+        uint32_t va[CPI][R], vx[Sh::BOTH ? CPI : 1][R];
 #pragma unroll
-        for (int r = 0; r < (1 << K); ++r) v[r] = shoup_mul(P.a[off + (uint64_t)r * C + col], kt.w, kt.wp, p);
+        for (int c = 0; c < CPI; ++c) {
+            const uint32_t col = col0 + c * kBThreads;
 #pragma unroll
-        for (int l = 0; l < K; ++l) {
-            const int h = (1 << K) >> (l + 1);
+            for (int r = 0; r < R; ++r) va[c][r] = P.a[off + (uint64_t)r * C + col];
+            if constexpr (Sh::BOTH) {
 #pragma unroll
-            for (int j = 0; j < (1 << l); ++j)
-#pragma unroll
-                for (int i = 0; i < h; ++i) bfly_row(v[(j << (K - l)) + i], v[(j << (K - l)) + i + h], FT[(1 << l) + j], p, p2);
+                for (int r = 0; r < R; ++r) vx[c][r] = P.x[off + (uint64_t)r * C + col];
+            }
         }
 #pragma unroll
-        for (int r = 0; r < (1 << K); ++r) P.c[off + (uint64_t)r * C + col] = v[r];
+        for (int c = 0; c < CPI; ++c) {
+            const uint32_t col = col0 + c * kBThreads;
+            uint32_t *v = va[c];
 #pragma unroll
-        for (int r = 0; r < (1 << K); ++r) v[r] = P.x[off + (uint64_t)r * C + col];
+            for (int r = 0; r < R; ++r) v[r] = shoup_mul(v[r], kt.w, kt.wp, p);
 #pragma unroll
-        for (int l = 0; l < K; ++l) {
-            const int h = (1 << K) >> (l + 1);
+            for (int l = 0; l < K; ++l) {
+                const int h = R >> (l + 1);
 #pragma unroll
-            for (int j = 0; j < (1 << l); ++j)
+                for (int j = 0; j < (1 << l); ++j)
 #pragma unroll
-                for (int i = 0; i < h; ++i) bfly_vec(v[(j << (K - l)) + i], v[(j << (K - l)) + i + h], FT[(1 << l) + j], p, p2);
+                    for (int i = 0; i < h; ++i)
+                        bfly_row(v[(j << (K - l)) + i], v[(j << (K - l)) + i + h], FT[(1 << l) + j], p, p2);
+            }
+#pragma unroll
+            for (int r = 0; r < R; ++r) P.c[off + (uint64_t)r * C + col] = v[r];
+            uint32_t *w = vx[Sh::BOTH ? c : 0];
+            if constexpr (!Sh::BOTH) {
+#pragma unroll
+                for (int r = 0; r < R; ++r) w[r] = P.x[off + (uint64_t)r * C + col];
+            }
+#pragma unroll
+            for (int l = 0; l < K; ++l) {
+                const int h = R >> (l + 1);
+#pragma unroll
+                for (int j = 0; j < (1 << l); ++j)
+#pragma unroll
+                    for (int i = 0; i < h; ++i)
+                        bfly_vec(w[(j << (K - l)) + i], w[(j << (K - l)) + i + h], FT[(1 << l) + j], p, p2);
+            }
+#pragma unroll
+            for (int r = 0; r < R; ++r) P.xs[off + (uint64_t)r * C + col] = w[r];
         }
-#pragma unroll
-        for (int r = 0; r < (1 << K); ++r) P.xs[off + (uint64_t)r * C + col] = v[r];
     }
 }
 
 template <int K>
 __device__ void cols_rec(const BatchParams &P, uint64_t off, uint32_t C, const Tw *FIT)
 {
+    using Sh = ColsShape<K>;
+    constexpr int R = Sh::R, CPI = Sh::CPI_REC;
     const uint32_t p = P.p, p2 = 2 * P.p;
-    for (uint32_t col = threadIdx.x; col < C; col += kBThreads) {
-        uint32_t v[1 << K];
+    for (uint32_t col0 = threadIdx.x; col0 < C; col0 += kBThreads * CPI) {
+        uint32_t v[CPI][R];
 #pragma unroll
-        for (int r = 0; r < (1 << K); ++r) v[r] = P.c[off + (uint64_t)r * C + col];
+        for (int c = 0; c < CPI; ++c) {
+            const uint32_t col = col0 + c * kBThreads;
 #pragma unroll
-        for (int l = K - 1; l >= 0; --l) {
-            const int h = (1 << K) >> (l + 1);
-#pragma unroll
-            for (int j = 0; j < (1 << l); ++j)
-#pragma unroll
-                for (int i = 0; i < h; ++i) bfly_rec(v[(j << (K - l)) + i], v[(j << (K - l)) + i + h], FIT[(1 << l) + j], p, p2);
+            for (int r = 0; r < R; ++r) v[c][r] = P.c[off + (uint64_t)r * C + col];
         }
 #pragma unroll
-        for (int r = 0; r < (1 << K); ++r) P.c[off + (uint64_t)r * C + col] = reduce_once(v[r], p);
+        for (int c = 0; c < CPI; ++c) {
+            const uint32_t col = col0 + c * kBThreads;
+#pragma unroll
+            for (int l = K - 1; l >= 0; --l) {
+                const int h = R >> (l + 1);
+#pragma unroll
+                for (int j = 0; j < (1 << l); ++j)
+#pragma unroll
+                    for (int i = 0; i < h; ++i)
+                        bfly_rec(v[c][(j << (K - l)) + i], v[c][(j << (K - l)) + i + h], FIT[(1 << l) + j], p, p2);
+            }
+#pragma unroll
+            for (int r = 0; r < R; ++r) P.c[off + (uint64_t)r * C + col] = reduce_once(v[c][r], p);
+        }
     }
 }
 
