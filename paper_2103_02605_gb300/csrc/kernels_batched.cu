@@ -324,7 +324,7 @@ __device__ void process(const BatchParams &P, uint32_t inst, BSmem &S)
     __syncthreads();
 }
 
-__global__ void __launch_bounds__(kBThreads, 2) k_bmain(const __grid_constant__ BatchParams P)
+__global__ void __launch_bounds__(kBThreads, 4) k_bmain(const __grid_constant__ BatchParams P)
 {
     __shared__ __align__(16) BSmem S;
     for (;;) {
