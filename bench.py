@@ -507,7 +507,7 @@ def run_extras(F, I, dev, stream):
                                                               bslots, 12)
     out["complex_fwd_bwd_4096x1024"]["roofline"] = R(out["complex_fwd_bwd_4096x1024"]["fused_ms"],
                                                                    4096 * 1024, None, 64, 3 * (3 * 9 * 5 + 17),
-                                                                   bound="shared-memory bandwidth (ncu)")
+                                                                   bound="shared-memory latency and issue (ncu)")
     out["gfp2_10000x2048"]["roofline"] = R(out["gfp2_10000x2048"]["ms"], 10000 * 2048, None, 24,
                                                          bound="alu (ncu)")
     out["ssa_K128_20000x256"]["roofline"] = R(out["ssa_K128_20000x256"]["ms"], 20000 * 256, None, 72,

@@ -250,6 +250,71 @@ __device__ __forceinline__ void cleaf_stage(SideT<T, TW> &sd, int t)
     for (int i = 0; i < 8; ++i) sd.ra(8 * t + i) = r[i];
 }
 
+// Stage 0 on the elements a thread loads from global memory: its groups are
+// g = h + G i (i < 2^NL) of the numbers t + (n/8) k, k = 0..7, in r[k], x[k]
+// (for every n >= 16, stage 0's element set is exactly that load set).  The
+// results go to shared memory for stage 1 or the last stage.
+template <int M, class T, class TW>
+__device__ __forceinline__ void cfwd_stage0_regs(SideT<T, TW> &sd, int t, T *r, T *x)
+{
+    using Sh = CShape<M>;
+    constexpr int NL = Sh::nl(0), G = 8 >> NL, MM = 1 << NL;
+#pragma unroll
+    for (int d = 0; d < NL; ++d) {
+        const int hh = MM >> (d + 1);
+#pragma unroll
+        for (int j = 0; j < (1 << d); ++j) {
+            const TW s = ld_tw(&sd.tw[(1 << d) + j]);
+#pragma unroll
+            for (int h = 0; h < G; ++h)
+#pragma unroll
+                for (int i = 0; i < hh; ++i) {
+                    const int lo = h + G * ((j << (NL - d)) + i), hi = lo + G * hh;
+                    const T tr = cmul(s, r[hi]);
+                    const T tx = cmul(s, x[lo]);
+                    r[hi] = csub(r[lo], tr);
+                    r[lo] = cadd(r[lo], tr);
+                    const T xh = x[hi];
+                    x[hi] = csub(tx, xh);
+                    x[lo] = cadd(tx, xh);
+                }
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        sd.ra(t + Sh::NTI * k) = r[k];
+        sd.xa(t + Sh::NTI * k) = x[k];
+    }
+}
+
+// The recombination of stage 0, ending in registers: r[k] receives the
+// result's number t + (n/8) k.
+template <int M, class T, class TW>
+__device__ __forceinline__ void crec_stage0_regs(SideT<T, TW> &sd, int t, T *r)
+{
+    using Sh = CShape<M>;
+    constexpr int NL = Sh::nl(0), G = 8 >> NL, MM = 1 << NL;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) r[k] = sd.ra(t + Sh::NTI * k);
+#pragma unroll
+    for (int d = NL - 1; d >= 0; --d) {
+        const int hh = MM >> (d + 1);
+#pragma unroll
+        for (int j = 0; j < (1 << d); ++j) {
+            const TW si = ld_tw(&sd.itw[(1 << d) + j]);
+#pragma unroll
+            for (int h = 0; h < G; ++h)
+#pragma unroll
+                for (int i = 0; i < hh; ++i) {
+                    const int lo = h + G * ((j << (NL - d)) + i), hi = lo + G * hh;
+                    const T sum = cadd(r[lo], r[hi]);
+                    r[hi] = csub(r[lo], r[hi]);
+                    r[lo] = cmul(sum, si);
+                }
+        }
+    }
+}
+
 // whole product for one instance: forward stages, last stage, recombination
 template <int M, int S, class T, class TW>
 __device__ __forceinline__ void cfwd_all(SideT<T, TW> &sd, int t)
@@ -261,13 +326,14 @@ __device__ __forceinline__ void cfwd_all(SideT<T, TW> &sd, int t)
     }
 }
 
-template <int M, int S, class T, class TW>
+// recombination stages S .. LOW (each followed by a barrier)
+template <int M, int S, class T, class TW, int LOW = 0>
 __device__ __forceinline__ void crec_all(SideT<T, TW> &sd, int t)
 {
-    if constexpr (S >= 0) {
+    if constexpr (S >= LOW) {
         crec_stage<M, S, T, TW>(sd, t);
         __syncthreads();
-        crec_all<M, S - 1, T, TW>(sd, t);
+        crec_all<M, S - 1, T, TW, LOW>(sd, t);
     }
 }
 
@@ -278,6 +344,25 @@ __device__ __forceinline__ void cproduct(SideT<T, TW> &sd, int t)
     cleaf_stage<M, T, TW>(sd, t);
     __syncthreads();
     crec_all<M, CShape<M>::NST - 1, T, TW>(sd, t);
+}
+
+// The same product with stage 0 on registers at both ends (n >= 16): the
+// inputs r[k], x[k] are the numbers t + (n/8) k of the row vector and the
+// vector, and r[k] receives the same numbers of the result.  Shared memory
+// need not hold the inputs; the caller's barriers: none before (each thread
+// writes only its own slots first), and every thread must have left the
+// product before shared memory is reused.
+template <int M, class T, class TW>
+__device__ __forceinline__ void cproduct_regs(SideT<T, TW> &sd, int t, T *r, T *x)
+{
+    static_assert(CShape<M>::NST >= 1, "n >= 16");
+    cfwd_stage0_regs<M, T, TW>(sd, t, r, x);
+    __syncthreads();
+    cfwd_all<M, 1, T, TW>(sd, t);
+    cleaf_stage<M, T, TW>(sd, t);
+    __syncthreads();
+    crec_all<M, CShape<M>::NST - 1, T, TW, 1>(sd, t);
+    crec_stage0_regs<M, T, TW>(sd, t, r);
 }
 
 template <int M>
@@ -291,6 +376,23 @@ __global__ void __launch_bounds__(CShape<M>::CT, 8) k_cfwd(const __grid_constant
     Side sd{csm + (size_t)li * 2 * Sh::N, csm + (size_t)li * 2 * Sh::N + Sh::N, P.tw, P.itw};
     const float2 *a = reinterpret_cast<const float2 *>(P.a) + inst * Sh::N;
     const float2 *x = reinterpret_cast<const float2 *>(P.x) + inst * Sh::N;
+    if constexpr (Sh::NST >= 1) {
+        // stage 0 on the loaded registers at both ends (cproduct_regs)
+        float2 r[8], xv[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            const int e = t + Sh::NTI * k;
+            r[k] = live ? a[e] : make_float2(0.f, 0.f);
+            xv[k] = live ? x[e] : make_float2(0.f, 0.f);
+        }
+        cproduct_regs<M, float2, float2>(sd, t, r, xv);
+        if (live) {
+            float2 *c = reinterpret_cast<float2 *>(P.c) + inst * Sh::N;
+#pragma unroll
+            for (int k = 0; k < 8; ++k) c[t + Sh::NTI * k] = make_float2(r[k].x * P.scale, r[k].y * P.scale);
+        }
+        return;
+    }
 #pragma unroll
     for (int k = 0; k < 8; ++k) {
         const int e = t + Sh::NTI * k;
@@ -393,6 +495,39 @@ __global__ void __launch_bounds__(CShape<M>::CT, 7) k_cbwd(const __grid_constant
     const float2 *x = reinterpret_cast<const float2 *>(P.x) + inst * Sh::N;
     const float2 *g = reinterpret_cast<const float2 *>(P.g) + inst * Sh::N;
     const float2 fc = make_float2(P.fc_re, P.fc_im);   // conj(f)
+    if constexpr (Sh::NST >= 1) {
+        // stage 0 on the loaded registers at both ends (cproduct_regs); g
+        // is read again for the second product instead of kept
+        const float2 z = make_float2(0.f, 0.f);
+        float2 r[8], xv[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            const int e = t + Sh::NTI * k;
+            // beta_e = conj(a_0) for e = 0, conj(f) conj(a_{n-e}) otherwise
+            const float2 ae = live ? a[e == 0 ? 0 : Sh::N - e] : z;
+            r[k] = e == 0 ? cconj(ae) : cmul(fc, cconj(ae));
+            xv[k] = live ? g[e] : z;
+        }
+        cproduct_regs<M, float2, float2>(sx, t, r, xv);
+        if (live) {
+            float2 *gx = reinterpret_cast<float2 *>(P.grad_x) + inst * Sh::N;
+#pragma unroll
+            for (int k = 0; k < 8; ++k) gx[t + Sh::NTI * k] = make_float2(r[k].x * P.scale, r[k].y * P.scale);
+        }
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            const int e = t + Sh::NTI * k;
+            r[k] = live ? g[e] : z;
+            xv[k] = live ? cconj(x[e]) : z;
+        }
+        cproduct_regs<M, float2, float2>(sa, t, r, xv);
+        if (live) {
+            float2 *ga = reinterpret_cast<float2 *>(P.grad_a) + inst * Sh::N;
+#pragma unroll
+            for (int k = 0; k < 8; ++k) ga[t + Sh::NTI * k] = make_float2(r[k].x * P.scale, r[k].y * P.scale);
+        }
+        return;
+    }
 #pragma unroll
     for (int k = 0; k < 8; ++k) {
         const int e = t + Sh::NTI * k;
