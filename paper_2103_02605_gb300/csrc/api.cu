@@ -930,7 +930,7 @@ struct BConfig {
 };
 const BConfig kBConfigs[] = {{1, 12}, {2, 12}, {3, 12}, {4, 12}, {1, 11}, {2, 11}, {3, 11}, {4, 11}};
 constexpr int kNumBConfigs = sizeof(kBConfigs) / sizeof(kBConfigs[0]);
-constexpr int kDefaultBConfig = 1;
+constexpr int kDefaultBConfig = 3;   // four CTAs per SM, 4096-residue tiles: the tuner's choice on GB300
 
 std::mutex g_tune_mu;
 std::map<std::tuple<int, uint32_t, uint32_t, uint64_t>, int> g_tune;   // (dev, p, count, total) -> config
