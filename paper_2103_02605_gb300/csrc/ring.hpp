@@ -15,6 +15,44 @@
 namespace fcirc {
 namespace host {
 
+FCIRC_HD uint64_t umulhi64(uint64_t a, uint64_t b)
+{
+#if defined(__CUDA_ARCH__)
+    return __umul64hi(a, b);
+#else
+    return (uint64_t)(((unsigned __int128)a * b) >> 64);
+#endif
+}
+
+// Products mod p < 2^31 by Barrett reduction with m = floor((2^64 - 1) / p):
+// for x = a b < p^2, q = floor(x m / 2^64) is floor(x / p) or one less
+// (x m / 2^64 > x / p - x (1 + 1/p) / 2^64 and x < 2^62), so x - q p lies in
+// [0, 2p) and one conditional subtraction finishes.  The reciprocal costs one
+// 64-bit division, once; each product is a multiply, a high multiply and a
+// subtraction -- on the GPU, much cheaper than a 64-bit remainder.
+struct ModP {
+    uint32_t p;
+    uint64_t m;
+    FCIRC_HD explicit ModP(uint32_t p_) : p(p_), m(~(uint64_t)0 / p_) {}
+    FCIRC_HD uint32_t mul(uint32_t a, uint32_t b) const
+    {
+        const uint64_t x = (uint64_t)a * b;
+        const uint64_t r = x - umulhi64(x, m) * p;
+        return (uint32_t)(r >= p ? r - p : r);
+    }
+    FCIRC_HD uint32_t pow(uint32_t b, uint64_t e) const
+    {
+        uint32_t r = 1 % p, x = b % p;
+        while (e) {
+            if (e & 1) r = mul(r, x);
+            x = mul(x, x);
+            e >>= 1;
+        }
+        return r;
+    }
+    FCIRC_HD uint32_t inv(uint32_t a) const { return pow(a, (uint64_t)p - 2); }   // p prime, a != 0
+};
+
 FCIRC_HD uint32_t mulmod(uint32_t a, uint32_t b, uint32_t p)
 {
     return (uint32_t)((uint64_t)a * b % p);
@@ -96,22 +134,29 @@ inline uint32_t omega(uint32_t p)
 
 // Discrete log of w in the cyclic group <Om> of order 2^v (Pohlig-Hellman,
 // one bit at a time).  Returns false if w is not in the group.
-FCIRC_HD bool dlog_2group(uint32_t w, uint32_t Om, int v, uint32_t p, uint64_t &out)
+FCIRC_HD bool dlog_2group(uint32_t w, uint32_t Om, int v, const ModP &M, uint64_t &out)
 {
-    if (powmod(w, (uint64_t)1 << v, p) != 1) return false;
-    uint32_t Om_inv = invmod(Om, p);
+    if (M.pow(w, (uint64_t)1 << v) != 1) return false;
+    uint32_t step = M.inv(Om);   // Om^-(2^i) at bit i
     uint64_t L = 0;
     uint32_t cur = w;  // w * Om^-L
     for (int i = 0; i < v; ++i) {
         // cur has order dividing 2^(v-i); test bit i
-        uint32_t t = powmod(cur, (uint64_t)1 << (v - 1 - i), p);
+        uint32_t t = cur;
+        for (int k = 0; k < v - 1 - i; ++k) t = M.mul(t, t);
         if (t != 1) {
             L |= (uint64_t)1 << i;
-            cur = mulmod(cur, powmod(Om_inv, (uint64_t)1 << i, p), p);
+            cur = M.mul(cur, step);
         }
+        step = M.mul(step, step);
     }
     out = L;
     return true;
+}
+
+FCIRC_HD bool dlog_2group(uint32_t w, uint32_t Om, int v, uint32_t p, uint64_t &out)
+{
+    return dlog_2group(w, Om, v, ModP(p), out);
 }
 
 // A 2^k-th root r of f mod p (r^(2^k) = f), or false if none exists.
@@ -119,8 +164,9 @@ FCIRC_HD bool dlog_2group(uint32_t w, uint32_t Om, int v, uint32_t p, uint64_t &
 // y^(2^k) = f * z for z = (f^q)^m in the 2-Sylow subgroup <Omega>; a 2^k-th
 // root of z^-1 there is Omega^(log/2^k) when 2^k divides the discrete log.
 // Same, with Omega and v supplied (usable on the device).
-FCIRC_HD bool nth_root_2k_om(uint32_t f, int k, uint32_t p, uint32_t Om, int v, uint32_t &root)
+FCIRC_HD bool nth_root_2k_om(uint32_t f, int k, const ModP &M, uint32_t Om, int v, uint32_t &root)
 {
+    const uint32_t p = M.p;
     f %= p;
     if (f == 0) return false;
     if (k == 0) { root = f; return true; }
@@ -134,26 +180,34 @@ FCIRC_HD bool nth_root_2k_om(uint32_t f, int k, uint32_t p, uint32_t Om, int v, 
         for (int i = 0; i < k; ++i) t = t * h % q;
         u = t;
     }
-    uint32_t y = powmod(f, u, p);
+    uint32_t y = M.pow(f, u);
     // z = y^(2^k) / f lies in <Omega>
     if (k > 62) return false;
-    uint32_t y2k = powmod(y, (uint64_t)1 << k, p);
-    uint32_t z = mulmod(y2k, invmod(f, p), p);
-    uint32_t zi = invmod(z, p);
+    uint32_t y2k = y;
+    for (int i = 0; i < k; ++i) y2k = M.mul(y2k, y2k);
+    uint32_t z = M.mul(y2k, M.inv(f));
+    uint32_t zi = M.inv(z);
     uint64_t L;
-    if (!dlog_2group(zi, Om, v, p, L)) return false;
+    if (!dlog_2group(zi, Om, v, M, L)) return false;
     uint32_t w;
     if (k <= v) {
         if (L & (((uint64_t)1 << k) - 1)) return false;
-        w = powmod(Om, L >> k, p);
+        w = M.pow(Om, L >> k);
     } else {
         // x -> x^(2^k) kills <Omega>; a root exists only if z = 1
         if (L != 0) return false;
         w = 1;
     }
-    root = mulmod(y, w, p);
-    if (powmod(root, (uint64_t)1 << k, p) != f) return false;
+    root = M.mul(y, w);
+    uint32_t chk = root;
+    for (int i = 0; i < k; ++i) chk = M.mul(chk, chk);
+    if (chk != f) return false;
     return true;
+}
+
+FCIRC_HD bool nth_root_2k_om(uint32_t f, int k, uint32_t p, uint32_t Om, int v, uint32_t &root)
+{
+    return nth_root_2k_om(f, k, ModP(p), Om, v, root);
 }
 
 inline bool nth_root_2k(uint32_t f, int k, uint32_t p, uint32_t &root)

@@ -12,6 +12,7 @@ static inline uint64_t __umul64hi(uint64_t a, uint64_t b) { return (uint64_t)(((
 #include "../../paper_2103_02605_gb300/csrc/modarith.cuh"
 #include "../../paper_2103_02605_gb300/csrc/gfp2.hpp"
 #include "../../paper_2103_02605_gb300/csrc/ssa.cuh"
+#include "../../paper_2103_02605_gb300/csrc/ring.hpp"
 
 using namespace fcirc;
 
@@ -59,7 +60,8 @@ int main()
                 printf("%u %u\n", r.re, r.im);
             }
         } else if (!strcmp(kind, "mod")) {
-            // mod <op> p w x y z ...: 32-bit arithmetic mod p (p < 2^30)
+            // mod <op> p w x y z ...: 32-bit arithmetic mod p (p < 2^30; the
+            // Barrett products take p < 2^31)
             unsigned p;
             scanf("%u", &p);
             const uint32_t p2 = 2 * p;
@@ -67,6 +69,22 @@ int main()
                 unsigned x, w;
                 scanf("%u %u", &x, &w);
                 printf("%u\n", shoup_mul(x, w, (uint32_t)(((uint64_t)w << 32) / p), p));
+            } else if (!strcmp(op, "barrett")) {
+                // the plan kernel's products and powers: ModP (ring.hpp)
+                unsigned a, b;
+                unsigned long long e;
+                scanf("%u %u %llu", &a, &b, &e);
+                const host::ModP M(p);
+                printf("%u %u\n", M.mul(a, b), M.pow(a, e));
+            } else if (!strcmp(op, "root")) {
+                // a 2^k-th root by the Barrett path, and by the plain path
+                unsigned f, Om;
+                int k, v;
+                scanf("%u %d %u %d", &f, &k, &Om, &v);
+                uint32_t r1 = 0, r2 = 0;
+                const bool o1 = host::nth_root_2k_om(f, k, host::ModP(p), Om, v, r1);
+                const bool o2 = host::nth_root_2k_om(f, k, p, Om, v, r2);
+                printf("%d %u %d %u\n", (int)o1, r1, (int)o2, r2);
             } else if (!strcmp(op, "redc")) {
                 unsigned long long t;
                 unsigned pinv;

@@ -141,3 +141,38 @@ def test_leaf_shift_costs_no_multiplication(harness, p):
         want.append(f"{lo[0]} {lo[1]} {hi[0]} {hi[1]}")
     for ln, w, o in zip(lines, want, harness(lines)):
         assert o.strip() == w, ln
+
+
+@pytest.mark.parametrize("p", PRIMES + (2 ** 31 - 1, 7681, 17))
+def test_barrett_products_of_the_plan_kernel(harness, p):
+    """ModP (ring.hpp), the products and powers the batched plan kernel
+    computes roots with: equal to exact integer arithmetic for random and
+    edge operands, including (p - 1)^2, the largest product."""
+    rng = random.Random(p + 7)
+    ops = [(0, 0, 0), (1, 1, 1), (p - 1, p - 1, p - 2), (p - 1, 1, 2 ** 40 + 3), (p // 2, p - 2, 0)]
+    ops += [(rng.randrange(p), rng.randrange(p), rng.randrange(2 ** 40)) for _ in range(600)]
+    out = harness([f"mod barrett {p} {a} {b} {e}" for a, b, e in ops])
+    for (a, b, e), o in zip(ops, out):
+        m, pw = map(int, o.split())
+        assert m == a * b % p and pw == pow(a, e, p), (a, b, e)
+
+
+@pytest.mark.parametrize("p", PRIMES)
+def test_roots_by_barrett_equal_the_plain_path(harness, p):
+    """nth_root_2k_om with the Barrett reducer finds the same root (or the
+    same absence of one) as with plain remainders, and the root is one:
+    r^(2^k) = f."""
+    v = ((p - 1) & -(p - 1)).bit_length() - 1
+    g = next(g for g in range(2, p) if all(pow(g, (p - 1) // r, p) != 1 for r in (2, 3, 5, 7, 17)
+                                              if (p - 1) % r == 0))
+    Om = pow(g, (p - 1) >> v, p)
+    rng = random.Random(p + 8)
+    cases = [(1, 3), (p - 1, 1), (p - 1, v), (Om, v), (Om, 1)]
+    cases += [(pow(rng.randrange(1, p), 2 ** k, p), k) for k in rng.choices(range(1, v), k=60)]
+    cases += [(rng.randrange(1, p), rng.randrange(1, v)) for _ in range(60)]   # mostly no root
+    out = harness([f"mod root {p} {f} {k} {Om} {v}" for f, k in cases])
+    for (f, k), o in zip(cases, out):
+        o1, r1, o2, r2 = map(int, o.split())
+        assert (o1, r1) == (o2, r2), (f, k)
+        if o1:
+            assert pow(r1, 2 ** k, p) == f % p, (f, k)
