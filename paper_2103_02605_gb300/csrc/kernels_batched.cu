@@ -66,7 +66,7 @@ __global__ void k_bplan(const BatchParams P)
             md.rhoi = M.inv(rho);
             const uint32_t two32 = (uint32_t)((1ull << 32) % P.p);
             const uint32_t kt = M.mul(two32, M.pow((P.p + 1) / 2, L));
-            md.kt = Tw{kt, host::shoup_quot(kt, P.p)};
+            md.kt = Tw{kt, M.quot32(kt)};
         }
         if (md.ok) bucket = kBMaxLog - m;
     }
@@ -99,24 +99,26 @@ __global__ void k_bscatter(const BatchParams P)
 
 // sigma_d = r^(2^(D-1-d)) and the same for ri, with their 64-bit Shoup
 // quotients, for d < D: the tile factors of plan.cu; thread d does level d.
-__device__ __forceinline__ void tile_factors(uint32_t r, uint32_t ri, int D, uint32_t p, uint32_t *sg)
+// (Barrett products and quotients, M: this runs before every tile of a large
+// instance while the CTA waits at the next barrier.)
+__device__ __forceinline__ void tile_factors(uint32_t r, uint32_t ri, int D, const host::ModP &M, uint32_t *sg)
 {
     const int d = threadIdx.x;
     if (d < D) {
         uint32_t s = r, si = ri;
         for (int k = 0; k < D - 1 - d; ++k) {
-            s = host::mulmod(s, s, p);
-            si = host::mulmod(si, si, p);
+            s = M.mul(s, s);
+            si = M.mul(si, si);
         }
         uint32_t *e = sg + d * 6;
         e[0] = s;
-        host::shoup_quot64(s, p, e[1], e[2]);
+        M.quot64(s, e[1], e[2]);
         e[3] = si;
-        host::shoup_quot64(si, p, e[4], e[5]);
+        M.quot64(si, e[4], e[5]);
     }
 }
 
-__device__ __forceinline__ Tw tw_of(uint32_t w, uint32_t p) { return Tw{w, host::shoup_quot(w, p)}; }
+__device__ __forceinline__ Tw tw_of(uint32_t w, const host::ModP &M) { return Tw{w, M.quot32(w)}; }
 
 // The top K levels of an instance of n = 2^m residues viewed as 2^K rows of
 // C = n / 2^K columns: forward on both sides (row vector into c, vector into
@@ -257,7 +259,7 @@ __device__ void run_tile(const BatchParams &P, const TileJob &J, uint64_t N, int
     }
 }
 
-__device__ void process(const BatchParams &P, uint32_t inst, BSmem &S)
+__device__ void process(const BatchParams &P, const host::ModP &M, uint32_t inst, BSmem &S)
 {
     const BatchMeta md = P.meta[inst];
     if (!md.ok) return;
@@ -265,7 +267,7 @@ __device__ void process(const BatchParams &P, uint32_t inst, BSmem &S)
     const uint64_t off = P.offsets[inst];
     const int m = md.m;
     if (m == 0) {
-        if (threadIdx.x == 0) P.c[off] = host::mulmod(P.a[off] % p, P.x[off] % p, p);
+        if (threadIdx.x == 0) P.c[off] = M.mul(P.a[off] % p, P.x[off] % p);
         return;
     }
     TileJob J;
@@ -277,13 +279,13 @@ __device__ void process(const BatchParams &P, uint32_t inst, BSmem &S)
     J.rho = nullptr;
     if (m <= P.big_log) {
         // one tile: factors of all L levels, leaf parameter rho when L = 0
-        tile_factors(md.rho, md.rhoi, m - 1, p, S.sg);
+        tile_factors(md.rho, md.rhoi, m - 1, M, S.sg);
         __syncthreads();
         J.a = Src{P.a + off, (uint64_t)1 << m, SRC_U32, 1, md.kt};
         J.x = Src{P.x + off, (uint64_t)1 << m, SRC_U32, 0, Tw{0, 0}};
         J.dst = P.c + off;
         J.store_lazy = 0;
-        run_tile(P, J, (uint64_t)1 << m, m, S.sg, tw_of(md.rho, p), S);
+        run_tile(P, J, (uint64_t)1 << m, m, S.sg, tw_of(md.rho, M), S);
         __syncthreads();
         return;
     }
@@ -295,25 +297,25 @@ __device__ void process(const BatchParams &P, uint32_t inst, BSmem &S)
         const int l = 31 - __clz(tid);
         uint32_t r = md.rho, ri = md.rhoi;
         for (int k = 0; k < L - l - 1; ++k) {
-            r = host::mulmod(r, r, p);
-            ri = host::mulmod(ri, ri, p);
+            r = M.mul(r, r);
+            ri = M.mul(ri, ri);
         }
-        S.FT[tid] = tw_of(host::mulmod(r, P.U[tid], p), p);
-        S.FIT[tid] = tw_of(host::mulmod(ri, P.Ui[tid], p), p);
+        S.FT[tid] = tw_of(M.mul(r, P.U[tid]), M);
+        S.FIT[tid] = tw_of(M.mul(ri, P.Ui[tid]), M);
     }
     if (tid >= 32 && tid < 32 + (1 << K)) {
         // tile root rho_t = rho Psi^brv_K(t), Psi a primitive 2^L-th root of unity
         const int t = tid - 32;
-        const uint32_t Psi = host::powmod(P.Om, 1ull << (P.v - L), p);
+        const uint32_t Psi = M.pow(P.Om, 1ull << (P.v - L));
         const uint32_t b = host::bitrev(t, K);
-        S.RT[t] = host::mulmod(md.rho, host::powmod(Psi, b, p), p);
-        S.RTi[t] = host::mulmod(md.rhoi, host::powmod(host::invmod(Psi, p), b, p), p);
+        S.RT[t] = M.mul(md.rho, M.pow(Psi, b));
+        S.RTi[t] = M.mul(md.rhoi, M.pow(M.inv(Psi), b));
     }
     __syncthreads();
     cols_dispatch(P, K, true, off, C, S.FT, S.FIT, md.kt);
     __syncthreads();
     for (int t = 0; t < (1 << K); ++t) {
-        tile_factors(S.RT[t], S.RTi[t], logT - 1, p, S.sg);
+        tile_factors(S.RT[t], S.RTi[t], logT - 1, M, S.sg);
         __syncthreads();
         const uint64_t toff = off + (uint64_t)t * C;
         J.a = Src{P.c + toff, C, SRC_U32, 0, Tw{0, 0}};
@@ -330,13 +332,14 @@ __device__ void process(const BatchParams &P, uint32_t inst, BSmem &S)
 __global__ void __launch_bounds__(kBThreads, 4) k_bmain(const __grid_constant__ BatchParams P)
 {
     __shared__ __align__(16) BSmem S;
+    const host::ModP M(P.p);
     for (;;) {
         if (threadIdx.x == 0) S.w = atomicAdd(P.work, 1u);
         __syncthreads();
         const uint32_t w = S.w;
         __syncthreads();
         if (w >= P.count) break;
-        process(P, P.order[w], S);
+        process(P, M, P.order[w], S);
     }
 }
 

@@ -51,6 +51,23 @@ struct ModP {
         return r;
     }
     FCIRC_HD uint32_t inv(uint32_t a) const { return pow(a, (uint64_t)p - 2); }   // p prime, a != 0
+    // floor(x / p) for x < 2^62: the same estimate, one correction
+    FCIRC_HD uint64_t div(uint64_t x) const
+    {
+        uint64_t q = umulhi64(x, m);
+        if (x - q * p >= p) ++q;
+        return q;
+    }
+    // Shoup quotients: floor(w 2^32 / p), and floor(w 2^64 / p) as (hi, lo)
+    // (w < p < 2^30 keeps every dividend below 2^62)
+    FCIRC_HD uint32_t quot32(uint32_t w) const { return (uint32_t)div((uint64_t)w << 32); }
+    FCIRC_HD void quot64(uint32_t w, uint32_t &hi, uint32_t &lo) const
+    {
+        const uint64_t t = (uint64_t)w << 32;
+        const uint64_t q = div(t);
+        hi = (uint32_t)q;
+        lo = (uint32_t)div((t - q * p) << 32);
+    }
 };
 
 FCIRC_HD uint32_t mulmod(uint32_t a, uint32_t b, uint32_t p)

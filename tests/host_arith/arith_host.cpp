@@ -76,6 +76,14 @@ int main()
                 scanf("%u %u %llu", &a, &b, &e);
                 const host::ModP M(p);
                 printf("%u %u\n", M.mul(a, b), M.pow(a, e));
+            } else if (!strcmp(op, "bquot")) {
+                // Barrett quotients: floor(w 2^32 / p) and floor(w 2^64 / p)
+                unsigned w;
+                scanf("%u", &w);
+                const host::ModP M(p);
+                uint32_t hi, lo;
+                M.quot64(w, hi, lo);
+                printf("%u %u %u\n", M.quot32(w), hi, lo);
             } else if (!strcmp(op, "root")) {
                 // a 2^k-th root by the Barrett path, and by the plain path
                 unsigned f, Om;

@@ -176,3 +176,17 @@ def test_roots_by_barrett_equal_the_plain_path(harness, p):
         assert (o1, r1) == (o2, r2), (f, k)
         if o1:
             assert pow(r1, 2 ** k, p) == f % p, (f, k)
+
+
+@pytest.mark.parametrize("p", PRIMES + (7681, 17, 3))
+def test_barrett_shoup_quotients(harness, p):
+    """ModP's quotients (the batched kernel's twiddles and tile factors):
+    floor(w 2^32 / p) and floor(w 2^64 / p) exactly, for every w in a random
+    sample and at the edges 0, 1, p - 1."""
+    rng = random.Random(p + 9)
+    ws = sorted({0, 1, p - 1, p // 2} | {rng.randrange(p) for _ in range(500)})
+    out = harness([f"mod bquot {p} {w}" for w in ws])
+    for w, o in zip(ws, out):
+        q32, hi, lo = map(int, o.split())
+        assert q32 == (w << 32) // p, w
+        assert (hi << 32) | lo == (w << 64) // p, w
