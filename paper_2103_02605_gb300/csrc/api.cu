@@ -188,7 +188,7 @@ bool fwd_params(int pass, const FwdDesc *jd, int njobs, int jobs_per_cta, ColFwd
     P = ColFwdParams{};
     for (int k = 0; k < njobs; ++k)
         P.job[k] = ColFwdJob{jd[k].src, jd[k].dst, jd[k].pl->d_gtw + jd[k].pl->pass_goff[pass], jd[k].pl->p,
-                             jd[k].vec_side, jd[k].half};
+                             jd[k].vec_side, jd[k].half, jd[k].pl->d_gtwl + jd[k].pl->pass_loff[pass]};
     P.jobs_per_cta = jobs_per_cta;
     P.N = (uint32_t)sh.n;
     P.logn = sh.m;
@@ -234,7 +234,8 @@ bool inv_params(int pass, const InvDesc *jd, int nprime, int epi, uint64_t *dst6
     if (!fast_col_ok(l1 - l0, sh.m - l1)) return false;
     P = ColInvParams{};
     for (int q = 0; q < nprime; ++q)
-        P.job[q] = ColInvJob{jd[q].src, jd[q].dst, jd[q].pl->d_gitw + jd[q].pl->pass_goff[pass], jd[q].pl->p};
+        P.job[q] = ColInvJob{jd[q].src, jd[q].dst, jd[q].pl->d_gitw + jd[q].pl->pass_goff[pass], jd[q].pl->p,
+                             jd[q].pl->d_gitwl + jd[q].pl->pass_loff[pass]};
     P.nprime = nprime;
     P.N = (uint32_t)sh.n;
     P.logn = sh.m;

@@ -104,6 +104,13 @@ struct Plan {
     Tw *d_gtw = nullptr, *d_gitw = nullptr;
     int pass_goff[4] = {0};
     int stage_off[4][3] = {{0}};
+    // each pass's last stage again, ordered by slot pair (entry
+    // 2 ((slot / 2) ngb + group block) + slot % 2), for the four-column
+    // kernels: in that stage every thread has a group block of its own, and
+    // this layout makes a warp's 128-bit loads of one slot pair contiguous;
+    // offsets in entries
+    Tw *d_gtwl = nullptr, *d_gitwl = nullptr;
+    int pass_loff[4] = {0};
 };
 
 int get_plan(uint32_t p, uint32_t f, uint64_t n, const Plan **out);

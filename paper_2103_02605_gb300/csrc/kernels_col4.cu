@@ -310,15 +310,48 @@ __device__ __forceinline__ void c4_level_tw(const Tw *g, Tw *t)
     }
 }
 
+// Where a group's twiddles come from.  TwGroup: the group-ordered table,
+// 16 consecutive entries per group block (128-bit loads).  TwSlots: the
+// copy of a stage ordered by slot pair (ColFwdJob::gtwl), entry
+// 2 (q stride + group block) + (slot & 1) for q = slot / 2 -- for the stage in
+// which every thread has a group block of its own, so that a warp's 128-bit
+// loads of one slot pair are contiguous.
+struct TwGroup {
+    const Tw *g;
+    template <int D>
+    __device__ __forceinline__ void level(Tw *t) const { c4_level_tw<D>(g, t); }
+};
+struct TwSlots {
+    const Tw *g;          // the group block's first entry (2 gb)
+    uint32_t stride;      // the stage's number of group blocks
+    template <int D>
+    __device__ __forceinline__ void level(Tw *t) const
+    {
+        // slot pair q of group block gb at entry 2 (q stride + gb)
+        constexpr int Q0 = 8 - (1 << D);
+        if constexpr (D == 0) {
+            const uint2 w = __ldg(reinterpret_cast<const uint2 *>(g + 2 * Q0 * stride));
+            t[0] = Tw{w.x, w.y};
+        } else {
+#pragma unroll
+            for (int k = 0; k < (1 << (D - 1)); ++k) {
+                const uint4 w = __ldg(reinterpret_cast<const uint4 *>(g + 2 * (uint32_t)(Q0 + k) * stride));
+                t[2 * k] = Tw{w.x, w.y};
+                t[2 * k + 1] = Tw{w.z, w.w};
+            }
+        }
+    }
+};
+
 // Forward levels D .. NL-1 of one group held as v[4 i + c] (row i, column
 // c); `cur` holds level D's twiddles, level D+1's are loaded before level D
 // is computed.
-template <int NL, int D, bool VEC>
-__device__ __forceinline__ void c4_fwd(uint32_t *v, const Tw *g, const Tw *cur, uint32_t p, uint32_t p2)
+template <int NL, int D, bool VEC, class TA>
+__device__ __forceinline__ void c4_fwd(uint32_t *v, const TA &g, const Tw *cur, uint32_t p, uint32_t p2)
 {
     if constexpr (D < NL) {
         Tw nxt[(D + 1 < NL) ? (2 << D) : 1];
-        if constexpr (D + 1 < NL) c4_level_tw<D + 1>(g, nxt);
+        if constexpr (D + 1 < NL) g.template level<D + 1>(nxt);
         constexpr int h = (1 << NL) >> (D + 1);
 #pragma unroll
         for (int j = 0; j < (1 << D); ++j)
@@ -334,18 +367,18 @@ __device__ __forceinline__ void c4_fwd(uint32_t *v, const Tw *g, const Tw *cur, 
                         bfly_row<false>(v[4 * lo + c], v[4 * (lo + h) + c], cur[j], p, p2);
                 }
             }
-        c4_fwd<NL, D + 1, VEC>(v, g, nxt, p, p2);
+        c4_fwd<NL, D + 1, VEC, TA>(v, g, nxt, p, p2);
     }
 }
 
 // Recombination levels D .. 0 of one group (inverse twiddles), with the
 // same one-level look-ahead of twiddle loads.
-template <int NL, int D>
-__device__ __forceinline__ void c4_rec(uint32_t *v, const Tw *g, const Tw *cur, uint32_t p, uint32_t p2)
+template <int NL, int D, class TA>
+__device__ __forceinline__ void c4_rec(uint32_t *v, const TA &g, const Tw *cur, uint32_t p, uint32_t p2)
 {
     if constexpr (D >= 0) {
         Tw nxt[D > 0 ? (1 << (D - 1)) : 1];
-        if constexpr (D > 0) c4_level_tw<D - 1>(g, nxt);
+        if constexpr (D > 0) g.template level<D - 1>(nxt);
         constexpr int h = (1 << NL) >> (D + 1);
 #pragma unroll
         for (int j = 0; j < (1 << D); ++j)
@@ -355,7 +388,7 @@ __device__ __forceinline__ void c4_rec(uint32_t *v, const Tw *g, const Tw *cur, 
 #pragma unroll
                 for (int c = 0; c < 4; ++c) bfly_rec(v[4 * lo + c], v[4 * (lo + h) + c], cur[j], p, p2);
             }
-        c4_rec<NL, D - 1>(v, g, nxt, p, p2);
+        c4_rec<NL, D - 1, TA>(v, g, nxt, p, p2);
     }
 }
 
@@ -439,10 +472,18 @@ __device__ __forceinline__ void c4fwd_stage(const ColFwdJob &J, const ColFwdPara
     for (int hb = 0; hb < B; ++hb) {
         int quad, row0, blk;
         c4_group<LF, D0, NL>(tid, hb, quad, row0, blk);
-        const Tw *g = gt + (((pb << D0) + blk) << 4);
+        const uint32_t gb = (pb << D0) + blk;
+        // the last stage gives every thread a group block of its own: its
+        // twiddles come from the slot-major copy
+        const auto g = [&] {
+            if constexpr (S == Sh::NST - 1)
+                return TwSlots{J.gtwl + 2 * gb, 1u << (P.l0 + D0)};
+            else
+                return TwGroup{gt + (gb << 4)};
+        }();
         constexpr int DS = (FIRST && half != 0) ? 1 : 0;
         Tw t0[1 << DS];
-        c4_level_tw<DS>(g, t0);
+        g.template level<DS>(t0);
         uint32_t *vg = v + 4 * hb * M;
         if constexpr (FIRST) {
 #pragma unroll
@@ -611,9 +652,17 @@ __device__ __forceinline__ void c4inv_job(const ColInvParams &P, const ColInvJob
         for (int hb = 0; hb < B; ++hb) {
             int quad, row0, blk;
             c4_group<LF, D0, NL>(tid, hb, quad, row0, blk);
-            const Tw *g = gt + (((pb << D0) + blk) << 4);
+            const uint32_t gb = (pb << D0) + blk;
+            // the first stage gives every thread a group block of its own:
+            // its twiddles come from the slot-major copy
+            const auto g = [&] {
+                if constexpr (FIRST)
+                    return TwSlots{J.gitwl + 2 * gb, 1u << (P.l0 + D0)};
+                else
+                    return TwGroup{gt + (gb << 4)};
+            }();
             Tw tl[1 << (NL - 1)];
-            c4_level_tw<NL - 1>(g, tl);
+            g.template level<NL - 1>(tl);
             c4_rec<NL, NL - 1>(v + 4 * hb * M, g, tl, p, p2);
         }
         // the last stage leaves canonical residues unless the output stays lazy

@@ -162,6 +162,10 @@ struct ColFwdJob {
     uint32_t p;
     int vec_side;
     int half;              // 0; 1: input zero below N/2; 2: input zero from N/2 (and s = 1 at level 0)
+    // the pass's last stage ordered by slot pair (Plan::d_gtwl): entry
+    // 2 ((slot / 2) ngb + gb) + slot % 2 for the ngb = 2^(l0 + d0) group
+    // blocks of that stage; the four-column kernels read that stage from here
+    const Tw *gtwl;
 };
 
 struct ColFwdParams {
@@ -180,6 +184,7 @@ struct ColInvJob {
     uint32_t *dst;
     const Tw *gitw;
     uint32_t p;
+    const Tw *gitwl;       // the last stage by slot pair (see ColFwdJob::gtwl)
 };
 
 struct ColInvParams {

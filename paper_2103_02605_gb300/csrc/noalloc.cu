@@ -52,7 +52,7 @@ struct HostPlan {
     uint32_t pinv;
     Tw kt;
     std::vector<uint32_t> U, Ui, sig;
-    std::vector<Tw> ftw, fitw, g, gi, rho;
+    std::vector<Tw> ftw, fitw, g, gi, gl, gil, rho;
 };
 
 Tw tw_of(uint32_t w, uint32_t p)
@@ -140,6 +140,17 @@ int build_host_plan(uint32_t p, uint32_t f, uint64_t n, HostPlan &h)
                     }
             off += (int)(ngb * 16);
         }
+        // the last stage again, ordered by slot pair (ColFwdJob::gtwl)
+        const int st = col_nstage(lf) - 1;
+        const uint64_t ngb = (uint64_t)1 << col_d0(lf, st);
+        h.gl.assign(ngb * 16, Tw{0, 0});
+        h.gil.assign(ngb * 16, Tw{0, 0});
+        for (uint64_t gb = 0; gb < ngb; ++gb)
+            for (int slot = 0; slot < 16; ++slot) {
+                const uint64_t e = 2 * ((uint64_t)(slot >> 1) * ngb + gb) + (slot & 1);
+                h.gl[e] = h.g[h.stage_off[0][st] + gb * 16 + slot];
+                h.gil[e] = h.gi[h.stage_off[0][st] + gb * 16 + slot];
+            }
     }
     // tile factors sigma_{t,d} = rho_t^(2^(D-1-d)), rho_t = rho psi_{2^L}^brv_k(t)
     const size_t ntile = (size_t)1 << h.k;
@@ -166,7 +177,7 @@ int build_host_plan(uint32_t p, uint32_t f, uint64_t n, HostPlan &h)
 // Device pointers of the tables inside the array.
 struct DevTables {
     uint32_t *U, *Ui, *sig;
-    Tw *ftw, *fitw, *g, *gi, *rho;
+    Tw *ftw, *fitw, *g, *gi, *gl, *gil, *rho;
 };
 
 // Per-device state: the array's device address (looked up once per device)
@@ -200,6 +211,8 @@ int upload_tables(unsigned char *base, const HostPlan &h, DevTables &t, cudaStre
     t.fitw = reinterpret_cast<Tw *>(carve(h.fitw.size() * sizeof(Tw)));
     t.g = reinterpret_cast<Tw *>(carve(h.g.size() * sizeof(Tw)));
     t.gi = reinterpret_cast<Tw *>(carve(h.gi.size() * sizeof(Tw)));
+    t.gl = reinterpret_cast<Tw *>(carve(h.gl.size() * sizeof(Tw)));
+    t.gil = reinterpret_cast<Tw *>(carve(h.gil.size() * sizeof(Tw)));
     if (off > kNoallocBytes)
         return fail(FCIRC_EINVAL, "fcirc_matvec_noalloc: plan tables exceed the static area");
     auto put = [&](void *dst, const void *src, size_t bytes) -> int {
@@ -214,6 +227,8 @@ int upload_tables(unsigned char *base, const HostPlan &h, DevTables &t, cudaStre
     FCIRC_TRY(put(t.fitw, h.fitw.data(), h.fitw.size() * sizeof(Tw)));
     FCIRC_TRY(put(t.g, h.g.data(), h.g.size() * sizeof(Tw)));
     FCIRC_TRY(put(t.gi, h.gi.data(), h.gi.size() * sizeof(Tw)));
+    FCIRC_TRY(put(t.gl, h.gl.data(), h.gl.size() * sizeof(Tw)));
+    FCIRC_TRY(put(t.gil, h.gil.data(), h.gil.size() * sizeof(Tw)));
     // copies from pageable memory have consumed their source when they return
     return FCIRC_OK;
 }
@@ -281,7 +296,7 @@ extern "C" int fcirc_matvec_noalloc(uint32_t p, uint32_t f, const uint32_t *a, c
         FCIRC_TRY(build_host_plan(p, f, n, hp));
         FCIRC_TRY(upload_tables(ds.base, hp, ds.t, s));
         hp.U.clear(); hp.Ui.clear(); hp.sig.clear(); hp.ftw.clear(); hp.fitw.clear();
-        hp.g.clear(); hp.gi.clear(); hp.rho.clear();
+        hp.g.clear(); hp.gi.clear(); hp.gl.clear(); hp.gil.clear(); hp.rho.clear();
         ds.h = hp;
         ds.p = p;
         ds.f = f % p;
@@ -316,8 +331,8 @@ extern "C" int fcirc_matvec_noalloc(uint32_t p, uint32_t f, const uint32_t *a, c
     const int lf = h.k;
     if (fast_col_ok(lf, h.m - lf)) {
         ColFwdParams fp{};
-        fp.job[0] = ColFwdJob{sa, c, t.g, p, 0, 0};
-        fp.job[1] = ColFwdJob{sx, xs, t.g, p, 1, 0};
+        fp.job[0] = ColFwdJob{sa, c, t.g, p, 0, 0, t.gl};
+        fp.job[1] = ColFwdJob{sx, xs, t.g, p, 1, 0, t.gl};
         fp.jobs_per_cta = 1;
         fp.N = (uint32_t)n;
         fp.logn = h.m;
@@ -345,7 +360,7 @@ extern "C" int fcirc_matvec_noalloc(uint32_t p, uint32_t f, const uint32_t *a, c
                                    : launch_tile(tp, (uint64_t)1 << h.k, 1, s));
     if (fast_col_ok(lf, h.m - lf)) {
         ColInvParams ip{};
-        ip.job[0] = ColInvJob{c, c, t.gi, p};
+        ip.job[0] = ColInvJob{c, c, t.gi, p, t.gil};
         ip.nprime = 1;
         ip.N = (uint32_t)n;
         ip.logn = h.m;

@@ -401,6 +401,25 @@ static int build_plan(uint32_t p, uint32_t f, uint64_t n, Plan *pl)
         }
         FCIRC_TRY(upload((void **)&pl->d_gtw, g.data(), g.size() * sizeof(Tw)));
         FCIRC_TRY(upload((void **)&pl->d_gitw, gi.data(), gi.size() * sizeof(Tw)));
+        // the last stage of each pass, ordered by slot pair
+        std::vector<Tw> gl, gil;
+        for (int i = 0; i < pl->npass; ++i) {
+            const int l0 = pl->pass_l0[i], lf = pl->pass_l1[i] - l0, st = col_nstage(lf) - 1;
+            const uint64_t ngb = (uint64_t)1 << (l0 + col_d0(lf, st));
+            pl->pass_loff[i] = (int)gl.size();
+            gl.resize(gl.size() + ngb * 16, Tw{0, 0});
+            gil.resize(gil.size() + ngb * 16, Tw{0, 0});
+            const Tw *G = g.data() + pl->pass_goff[i] + pl->stage_off[i][st];
+            const Tw *GI = gi.data() + pl->pass_goff[i] + pl->stage_off[i][st];
+            for (uint64_t gb = 0; gb < ngb; ++gb)
+                for (int slot = 0; slot < 16; ++slot) {
+                    const uint64_t e = 2 * ((uint64_t)(slot >> 1) * ngb + gb) + (slot & 1);
+                    gl[pl->pass_loff[i] + e] = G[gb * 16 + slot];
+                    gil[pl->pass_loff[i] + e] = GI[gb * 16 + slot];
+                }
+        }
+        FCIRC_TRY(upload((void **)&pl->d_gtwl, gl.data(), gl.size() * sizeof(Tw)));
+        FCIRC_TRY(upload((void **)&pl->d_gitwl, gil.data(), gil.size() * sizeof(Tw)));
     }
     // ---- tile factors: rho_t = rho * Psi^brv_k(t), sigma_{t,d} = rho_t^(2^(D-1-d))
     {
@@ -446,6 +465,8 @@ static void free_plan_tables(Plan *pl)
     cudaFree(pl->d_rho);
     cudaFree(pl->d_gtw);
     cudaFree(pl->d_gitw);
+    cudaFree(pl->d_gtwl);
+    cudaFree(pl->d_gitwl);
 }
 
 int get_plan(uint32_t p, uint32_t f, uint64_t n, const Plan **out)
