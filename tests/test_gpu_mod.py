@@ -225,14 +225,26 @@ def test_matvec_config0_full(F, orc):
 
 
 def test_matvec_extreme_values(F, orc):
-    for m in (1, 5, 12, 14):
-        n = 1 << m
-        a = np.full(n, P1 - 1, np.uint32)
-        x = np.full(n, P1 - 1, np.uint32)
-        for f in (1, P1 - 1):
-            assert np.array_equal(matvec(F, P1, f, a, x), orc.fcirc_matvec_mod(P1, f, a, x))
-        z = np.zeros(n, np.uint32)
-        assert not matvec(F, P1, 3 ** 2 if m == 1 else 1, z, x).any()
+    """Every entry p - 1, for the three primes: each has its own schedule of
+    reductions in the tile kernel (room 4, 9 and 25 times p below 2^32)."""
+    rng = np.random.default_rng(17)
+    for p in (P1, P2, P3):
+        for m in (1, 5, 12, 14, 16, 20):
+            n = 1 << m
+            a = np.full(n, p - 1, np.uint32)
+            x = np.full(n, p - 1, np.uint32)
+            for f in (1, p - 1):
+                got = matvec(F, p, f, a, x)
+                if m <= 14:
+                    assert np.array_equal(got, orc.fcirc_matvec_mod(p, f, a, x)), (p, m, f)
+                else:
+                    rows = np.unique(np.concatenate([np.arange(8), n - 1 - np.arange(8),
+                                                     rng.integers(0, n, 48)])).astype(np.uint64)
+                    assert np.array_equal(got[rows.astype(np.int64)], orc.fcirc_matvec_mod_rows(p, f, a, x, rows)), \
+                        (p, m, f)
+            if p == P1:
+                z = np.zeros(n, np.uint32)
+                assert not matvec(F, P1, 3 ** 2 if m == 1 else 1, z, x).any()
 
 
 def test_matvec_host_buffers_match_device(F, orc):
