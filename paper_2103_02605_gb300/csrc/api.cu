@@ -206,6 +206,7 @@ int run_fwd_pass(int pass, const FwdDesc *jd, int njobs, int jobs_per_cta, cudaS
     ColFwdParams CP;
     if (fwd_params(pass, jd, njobs, jobs_per_cta, CP)) {
         CP.ilv = ilv;
+        FCIRC_TRY(fwd_tma_maps(CP, njobs, l1 - l0));
         return launch_colfwd(CP, njobs / jobs_per_cta, s);
     }
     if (ilv) return fail(FCIRC_EINVAL, "interleaved layout requested from a strided pass");

@@ -40,6 +40,7 @@
 #include "prof.hpp"
 #include "cluster.cuh"
 #include "tile_dev.cuh"
+#include "tma.cuh"
 
 namespace fcirc {
 
@@ -424,12 +425,27 @@ __device__ __forceinline__ void put4(uint32_t *v, uint4 w)
 
 __device__ __forceinline__ uint4 get4(const uint32_t *v) { return make_uint4(v[0], v[1], v[2], v[3]); }
 
+// Whether the interleaved output of this pass leaves through TMA tensor
+// stores: 12 levels, maps made (fwd_tma_maps), and shared memory on a
+// 128-byte boundary (the boxes).  The same for every thread.
+template <int LF, bool ILV>
+__device__ __forceinline__ bool c4_tma_st(const ColFwdParams &P, const uint32_t *sm)
+{
+    if constexpr (ILV && LF == 12)
+        return P.tma_st && (sm_u32(sm) & 127u) == 0;
+    else
+        return false;
+}
+
 // ILV: the pass writes the tile-pair interleaved layout; its last stage
-// stores straight from registers (no shared-memory write, no store phase).
+// stores straight from registers (no shared-memory write, no store phase),
+// or, for 12 levels, writes the CTA's 64 KB of shared memory as eight TMA
+// boxes and leaves the stores to the TMA unit while the next job starts
+// (tm: the job's tensor map).
 template <int LF, int S, int MODE, bool VEC, bool ILV>
 __device__ __forceinline__ void c4fwd_stage(const ColFwdJob &J, const ColFwdParams &P, uint32_t *sm,
                                             uint32_t base, uint32_t pb, int logS, int tid, bool wait_first,
-                                            int cache = C4_NOCACHE)
+                                            int cache = C4_NOCACHE, const CUtensorMap *tm = nullptr)
 {
     using Sh = C4<LF>;
     constexpr int NL = Sh::nl(S), D0 = Sh::d0(S);
@@ -519,6 +535,34 @@ __device__ __forceinline__ void c4fwd_stage(const ColFwdJob &J, const ColFwdPara
         static_assert(B == 1 && M == 16 && LST == 0, "last stage shape");
         int quad, row0, blk;
         c4_group<LF, D0, NL>(tid, 0, quad, row0, blk);
+        if constexpr (LF == 12) {
+            // (the CTA's 2^11 tile pairs inside the map's N / 8192)
+            if (c4_tma_st<LF, ILV>(P, sm) && (base >> 16) + 256u <= (P.N >> 16)) {
+                // every thread has read this stage's inputs from shared memory
+                __syncthreads();
+                // the thread's row pair 8 tid + k (its rows row0 = 16 tid ..
+                // row0 + 15, one quad per CTA) is sector tid of box k: byte
+                // 8192 k + 32 tid + 16 (row parity) of the 64 KB area
+                static_assert(Sh::LNQ == 0, "one column quad per CTA");
+#pragma unroll
+                for (int k = 0; k < 8; ++k)
+#pragma unroll
+                    for (int h = 0; h < 2; ++h)
+                        *reinterpret_cast<uint4 *>(sm + 2048 * k + 8 * tid + 4 * h) = get4(v + 8 * k + 4 * h);
+                fence_async_shared();
+                __syncthreads();
+                if (tid == 0) {
+                    // the CTA's column quad, and its first tile pair (base is
+                    // the natural index of its first element, rows of 4096) as
+                    // 8 t0: 2^11 tile pairs per CTA
+                    const int q = (int)((base & 4095u) >> 2), t0 = (int)(base >> 16);
+#pragma unroll
+                    for (int k = 0; k < 8; ++k) tma_store_5d(tm, sm + 2048 * k, 0, 0, q, k, t0);
+                    tma_store_commit();
+                }
+                return;
+            }
+        }
         uint32_t *d = J.dst + ilv_pos(base + ((uint32_t)quad << 2) + ((uint32_t)row0 << 12));
 #pragma unroll
         for (int k = 0; k < 8; ++k) st_sector(d + 8192 * k, v + 8 * k);
@@ -527,10 +571,13 @@ __device__ __forceinline__ void c4fwd_stage(const ColFwdJob &J, const ColFwdPara
     // the previous job's last stage (or store phase) may still read this
     // CTA's shared memory
     if (FIRST && wait_first) {
-        if constexpr (ILV)
+        if constexpr (ILV) {
+            // and the previous job's TMA stores have read it
+            if (tid == 0 && c4_tma_st<LF, ILV>(P, sm)) tma_store_wait_read();
             __syncthreads();
-        else
+        } else {
             grp_wait<Sh::CL>();
+        }
     }
 #pragma unroll
     for (int hb = 0; hb < B; ++hb) {
@@ -553,19 +600,20 @@ __device__ __forceinline__ void c4fwd_jobs(const ColFwdParams &P, uint32_t *sm, 
 #pragma unroll 1
     for (int jj = 0; jj < P.jobs_per_cta; ++jj) {
         const ColFwdJob &J = P.job[j0 + jj];
+        const CUtensorMap *tm = &P.tmap[j0 + jj];
         c4fwd_stage<LF, 0, MODE, VEC, ILV>(J, P, sm, base, pb, logS, tid, jj > 0,
-                                           cached ? (jj == 0 ? C4_FILL : C4_USE) : C4_NOCACHE);
+                                           cached ? (jj == 0 ? C4_FILL : C4_USE) : C4_NOCACHE, tm);
         if constexpr (Sh::NST > 1) {
             __syncthreads();
-            c4fwd_stage<LF, 1, MODE, VEC, ILV>(J, P, sm, base, pb, logS, tid, false);
+            c4fwd_stage<LF, 1, MODE, VEC, ILV>(J, P, sm, base, pb, logS, tid, false, C4_NOCACHE, tm);
         }
         if constexpr (Sh::NST > 2) {
             __syncthreads();
-            c4fwd_stage<LF, 2, MODE, VEC, ILV>(J, P, sm, base, pb, logS, tid, false);
+            c4fwd_stage<LF, 2, MODE, VEC, ILV>(J, P, sm, base, pb, logS, tid, false, C4_NOCACHE, tm);
         }
         if constexpr (Sh::NST > 3) {
             __syncthreads();
-            c4fwd_stage<LF, 3, MODE, VEC, ILV>(J, P, sm, base, pb, logS, tid, false);
+            c4fwd_stage<LF, 3, MODE, VEC, ILV>(J, P, sm, base, pb, logS, tid, false, C4_NOCACHE, tm);
         }
         if constexpr (!ILV) {
             grp_arrive<Sh::CL>();
@@ -575,6 +623,8 @@ __device__ __forceinline__ void c4fwd_jobs(const ColFwdParams &P, uint32_t *sm, 
         }
     }
     if constexpr (!ILV) grp_wait<Sh::CL>();   // no CTA leaves while a peer still reads its shared memory
+    // nor while its own TMA stores still read it
+    if (tid == 0 && c4_tma_st<LF, ILV>(P, sm)) tma_store_wait_read();
 }
 
 // CTA origin: node pb of level l0 and the CTA's first column
@@ -593,7 +643,7 @@ template <int LF, int M0, int M1, bool ILV>
 __global__ void __cluster_dims__(ILV ? 1 : C4<LF>::CL, 1, 1) __launch_bounds__(kC4Threads, FCIRC_C4FWD_MINB)
     k_colfwd4(const __grid_constant__ ColFwdParams P)
 {
-    extern __shared__ __align__(16) uint32_t sm[];
+    extern __shared__ __align__(128) uint32_t sm[];
     uint32_t pb, base;
     int logS;
     c4_origin<LF>(P.logn, P.l0, P.l1, pb, base, logS);

@@ -177,7 +177,16 @@ struct ColFwdParams {
     int logn, l0, l1;
     int stage_off[3];
     int ilv;               // write the tile-pair interleaved layout (ilv_pos); col4_fwd_ilv_ok
+    // the interleaved output of a 12-level pass through TMA tensor stores
+    // (fwd_tma_maps): one map per job over its destination, boxes of one
+    // column quad of 256 row pairs 8 t + k, dense in shared memory
+    int tma_st;
+    CUtensorMap tmap[6];
 };
+
+// Tensor maps of the forward pass's interleaved destinations; sets
+// P.tma_st when every job's map could be made (tma_host.cu).
+int fwd_tma_maps(ColFwdParams &P, int njobs, int lf);
 
 struct ColInvJob {
     const uint32_t *src;

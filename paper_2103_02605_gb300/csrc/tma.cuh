@@ -72,6 +72,17 @@ __device__ __forceinline__ void tma_store_4d(const CUtensorMap *map, const void 
                  : "memory");
 }
 
+// Tiled 5-D store of one box from shared memory at src into `map` at
+// (c0, .., c4); tracked in the issuing thread's bulk group.
+__device__ __forceinline__ void tma_store_5d(const CUtensorMap *map, const void *src, int c0, int c1, int c2, int c3,
+                                             int c4)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.5d.global.shared::cta.tile.bulk_group [%0, {%2, %3, %4, %5, %6}], [%1];\n" ::"l"(map),
+        "r"(sm_u32(src)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(c4)
+        : "memory");
+}
+
 __device__ __forceinline__ void tma_store_commit() { asm volatile("cp.async.bulk.commit_group;\n" ::: "memory"); }
 
 // Waits until the committed stores have read their shared-memory sources

@@ -222,6 +222,34 @@ def test_interleave_address_identities_of_the_kernels():
                             _ilv_pos(o) + 8192 * k + 4 + c
 
 
+def test_forward_pass_tma_store_boxes():
+    """The 12-level forward pass's TMA stores (kernels_col4.cu,
+    fwd_tma_maps): shared-memory word 2048 k + 8 tid + 4 h + w of box k,
+    written with thread tid's rows 16 tid + 2 k + h, column w of its quad,
+    lands at the 5-D tensor {4, 2, 1024, 8, N / 65536} (strides 16, 32,
+    32 KiB, 256 KiB bytes) coordinate (w, h, q, k, t0 + tid): that must be
+    ilv_pos of the element's natural index, for every element of the CTA, and
+    inside the array."""
+    import numpy as np
+    tid = np.arange(256, dtype=np.int64)[:, None, None, None]
+    k = np.arange(8, dtype=np.int64)[None, :, None, None]
+    h = np.arange(2, dtype=np.int64)[None, None, :, None]
+    w = np.arange(4, dtype=np.int64)[None, None, None, :]
+    for N, pbs in ((1 << 24, (0,)), (1 << 26, (0, 1, 3))):
+        for pb in pbs:
+            for cg in (0, 1, 2, 511, 1023):
+                base = (pb << 24) + 4 * cg                    # c4_origin, l0 = log2(N) - 24
+                q, t0 = (base & 4095) >> 2, base >> 16
+                assert t0 + 256 <= N >> 16                    # the kernel's guard holds
+                coord = w * 1 + h * 4 + q * 8 + k * 8192 + (t0 + tid) * 65536
+                natural = base + ((16 * tid + 2 * k + h) << 12) + w
+                assert np.array_equal(coord, _ilv_pos(natural))
+                assert coord.min() >= 0 and coord.max() < N
+                # shared memory: the eight boxes tile the 64 KB area exactly once
+                smem = 2048 * k + 8 * tid + 4 * h + w
+                assert np.array_equal(np.sort(smem.ravel()), np.arange(16384))
+
+
 def _cpos(e):
     """Python restatement of cpos<T> for 8-byte elements (kernels_complex.cu)."""
     return e ^ (((e >> 4) & 7) | (((e >> 6) & 1) << 3))
