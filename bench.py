@@ -279,14 +279,15 @@ def kernel_bytes():
 # reports null.  The summaries in
 # profiles/ give the commands and the other counters.
 _KSRC = {
-    "k_colfwd4": ["kernels_col4.cu", "cluster.cuh", "tile_dev.cuh", "modarith.cuh", "kernels_mod.hpp"],
-    "k_colinv4x3": ["kernels_col4.cu", "cluster.cuh", "tile_dev.cuh", "modarith.cuh", "kernels_mod.hpp"],
-    "k_tile4096": ["kernels_tile.cu", "tile_dev.cuh", "tma.cuh", "modarith.cuh", "kernels_mod.hpp"],
+    "k_colfwd4": ["kernels_col4.cu", "cluster.cuh", "tile_dev.cuh", "tma.cuh", "tma_host.cu", "modarith.cuh",
+                  "kernels_mod.hpp"],
+    "k_colinv4x3": ["kernels_col4.cu", "cluster.cuh", "tile_dev.cuh", "tma.cuh", "modarith.cuh", "kernels_mod.hpp"],
+    "k_tile4096": ["kernels_tile.cu", "tile_dev.cuh", "tma.cuh", "tma_host.cu", "modarith.cuh", "kernels_mod.hpp"],
 }
 NCU_TRAFFIC = {
-    "k_colfwd4": (382039552, "28a3198ab4dfa901"),
-    "k_tile4096": (564267520, "1c365d591b51413b"),
-    "k_colinv4x3": (304484864, "28a3198ab4dfa901"),
+    "k_colfwd4": (385131264, "52e6bfa917e1237b"),
+    "k_tile4096": (563296256, "ca6914afd827ac5b"),
+    "k_colinv4x3": (304125440, "1718e74ab219e9fd"),
 }
 
 
