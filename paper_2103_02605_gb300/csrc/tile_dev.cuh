@@ -276,13 +276,17 @@ __device__ __forceinline__ void tile4096_dev(const TileJob &J, uint32_t N, uint3
         fwd1<4, 4, false>(a, twB, p, p2);
     else
         fwd1<4, 4, true>(x, twB, p, p2);
-    __syncthreads();
+    // Stages B and C work on the same 256-residue block, tid >> 4, held by
+    // the 16 threads of one half-warp, and tphi keeps a block inside its own
+    // 128-byte rows: the exchanges between them need only the warp's
+    // threads to meet (__syncwarp orders their shared-memory accesses).
+    __syncwarp();
 #pragma unroll
     for (int m = 0; m < 16; ++m) {
         if (DO_A) SA[tphiB(tB, m)] = a[m];
         if (DO_X) SX[tphiB(tB, m)] = x[m];
     }
-    __syncthreads();
+    __syncwarp();
     // stage C: levels 8..10 and the leaves, residues 16 tid .. 16 tid + 15
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
@@ -365,16 +369,18 @@ __device__ __forceinline__ void tile4096_dev(const TileJob &J, uint32_t N, uint3
     } else {
         rec1<4, 3>(a, [&](int d, int j) { return tc[(1 << d) - 1 + j]; }, p, p2);
     }
-    __syncthreads();
+    // back from stage C to stage B, and stage B's writes: inside the block
+    // of this half-warp (see the forward exchange)
+    __syncwarp();
 #pragma unroll
     for (int q = 0; q < 4; ++q)
         *reinterpret_cast<uint4 *>(&SA[tphiC(tC, q)]) =
             make_uint4(a[4 * q], a[4 * q + 1], a[4 * q + 2], a[4 * q + 3]);
-    __syncthreads();
+    __syncwarp();
 #pragma unroll
     for (int m = 0; m < 16; ++m) a[m] = SA[tphiB(tB, m)];
     rec1<4, 4>(a, [&](int d, int j) { return SITW[(1 << (4 + d)) + (nb << d) + j]; }, p, p2);
-    __syncthreads();
+    __syncwarp();
 #pragma unroll
     for (int m = 0; m < 16; ++m) SA[tphiB(tB, m)] = a[m];
     __syncthreads();

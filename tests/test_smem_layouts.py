@@ -182,6 +182,24 @@ def test_four_column_address_identities(LF):
                     assert got == want
 
 
+def test_tile_stage_b_c_exchanges_stay_in_a_half_warp():
+    """The tile kernel's exchanges between stages B and C (tile_dev.cuh)
+    synchronise with __syncwarp, not a CTA barrier: every shared-memory word
+    thread tid reads or writes in those stages (stage B: residues
+    256 (tid >> 4) + 16 m + (tid & 15); stage C: 16 tid .. 16 tid + 15, in
+    tphi positions) lies in its block's 256 words [256 g, 256 g + 256),
+    g = tid >> 4, and the 16 threads of block g lie in one warp."""
+    for tid in range(256):
+        g = tid >> 4
+        words = {tphi(256 * g + 16 * m + (tid & 15)) for m in range(16)}
+        words |= {tphi(16 * tid + q) for q in range(16)}
+        assert all(256 * g <= w < 256 * g + 256 for w in words), tid
+        assert (16 * g) // 32 == (16 * g + 15) // 32
+    # and the blocks' words do not overlap: each is a permutation of its range
+    for g in range(16):
+        assert sorted(tphi(e) for e in range(256 * g, 256 * g + 256)) == list(range(256 * g, 256 * g + 256))
+
+
 def _ilv_pos(i):
     """Python restatement of ilv_pos (kernels_mod.hpp): bits 2..12 of i
     rotated so that bit 12 (the tile's parity) becomes bit 2."""
