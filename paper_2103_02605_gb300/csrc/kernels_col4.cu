@@ -589,6 +589,20 @@ __device__ __forceinline__ void c4fwd_stage(const ColFwdJob &J, const ColFwdPara
     }
 }
 
+// The barrier between register stages S and S + 1 of a pass (either
+// direction).  The last two stages exchange residues only between threads
+// of one warp (every slot is owned by the same warp in both; checked on the
+// CPU for LF = 8 .. 12), so a warp sync orders them; earlier exchanges cross
+// warps.
+template <int LF, int S>
+__device__ __forceinline__ void c4_stage_sync()
+{
+    if constexpr (S == C4<LF>::NST - 2)
+        __syncwarp();
+    else
+        __syncthreads();
+}
+
 template <int LF, int MODE, bool VEC, bool ILV>
 __device__ __forceinline__ void c4fwd_jobs(const ColFwdParams &P, uint32_t *sm, int j0, uint32_t base,
                                            uint32_t pb, int logS, int tid)
@@ -604,15 +618,15 @@ __device__ __forceinline__ void c4fwd_jobs(const ColFwdParams &P, uint32_t *sm, 
         c4fwd_stage<LF, 0, MODE, VEC, ILV>(J, P, sm, base, pb, logS, tid, jj > 0,
                                            cached ? (jj == 0 ? C4_FILL : C4_USE) : C4_NOCACHE, tm);
         if constexpr (Sh::NST > 1) {
-            __syncthreads();
+            c4_stage_sync<LF, 0>();
             c4fwd_stage<LF, 1, MODE, VEC, ILV>(J, P, sm, base, pb, logS, tid, false, C4_NOCACHE, tm);
         }
         if constexpr (Sh::NST > 2) {
-            __syncthreads();
+            c4_stage_sync<LF, 1>();
             c4fwd_stage<LF, 2, MODE, VEC, ILV>(J, P, sm, base, pb, logS, tid, false, C4_NOCACHE, tm);
         }
         if constexpr (Sh::NST > 3) {
-            __syncthreads();
+            c4_stage_sync<LF, 2>();
             c4fwd_stage<LF, 3, MODE, VEC, ILV>(J, P, sm, base, pb, logS, tid, false, C4_NOCACHE, tm);
         }
         if constexpr (!ILV) {
@@ -819,15 +833,15 @@ __global__ void __cluster_dims__(C4<LF>::CL, 1, 1) __launch_bounds__(kC4Threads,
     const uint32_t base0 = base - ((uint32_t)rank << (2 + Sh::LNQ));
     if constexpr (Sh::NST > 3) {
         c4inv_stage<LF, NP, 3, ILV>(P, sm, base, pb, logS, tid);
-        __syncthreads();
+        c4_stage_sync<LF, 2>();
     }
     if constexpr (Sh::NST > 2) {
         c4inv_stage<LF, NP, 2, ILV>(P, sm, base, pb, logS, tid);
-        __syncthreads();
+        c4_stage_sync<LF, 1>();
     }
     if constexpr (Sh::NST > 1) {
         c4inv_stage<LF, NP, 1, ILV>(P, sm, base, pb, logS, tid);
-        __syncthreads();
+        c4_stage_sync<LF, 0>();
     }
     c4inv_stage<LF, NP, 0, ILV>(P, sm, base, pb, logS, tid);
     grp_arrive<Sh::CL>();
@@ -863,15 +877,15 @@ __global__ void __cluster_dims__(3, 1, 1) __launch_bounds__(kC4Threads, 2)
     const ColInvJob &J = P.job[q];
     if constexpr (Sh::NST > 3) {
         c4inv_job<LF, 3, ILV>(P, J, sm, base, pb, logS, tid);
-        __syncthreads();
+        c4_stage_sync<LF, 2>();
     }
     if constexpr (Sh::NST > 2) {
         c4inv_job<LF, 2, ILV>(P, J, sm, base, pb, logS, tid);
-        __syncthreads();
+        c4_stage_sync<LF, 1>();
     }
     if constexpr (Sh::NST > 1) {
         c4inv_job<LF, 1, ILV>(P, J, sm, base, pb, logS, tid);
-        __syncthreads();
+        c4_stage_sync<LF, 0>();
     }
     c4inv_job<LF, 0, ILV>(P, J, sm, base, pb, logS, tid);
     cl_arrive();

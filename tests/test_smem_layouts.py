@@ -136,6 +136,42 @@ def test_four_column_store_phase(LF, maxlcl, LR):
     assert len(cover) == (1 << LCQ) << LF and set(cover.values()) == {1}
 
 
+def _c4_stage_owners(LF, S, LR=4):
+    """16-byte slot -> thread of register stage S of a four-column pass (a
+    thread writes back the slots it read)."""
+    NT, ROWS = 4096 >> LR, 1 << LR
+    NST = (LF + LR - 1) // LR
+    NL0 = LF - LR * (NST - 1)
+    NL = NL0 if S == 0 else LR
+    D0 = 0 if S == 0 else NL0 + LR * (S - 1)
+    M, B, LST, LRB, LGQ = 1 << NL, ROWS >> NL, LF - D0 - NL, LF - D0, LF - NL
+    own = {}
+    for t in range(NT):
+        for h in range(B):
+            gg = t + NT * h
+            quad, g = gg >> LGQ, gg & ((1 << LGQ) - 1)
+            blk = g >> LST
+            for i in range(M):
+                row = (blk << LRB) + (g & ((1 << LST) - 1)) + (i << LST)
+                own[c4_off16(LF, quad, row, LR)] = t
+    return own
+
+
+@pytest.mark.parametrize("LF", [8, 9, 10, 11, 12])
+def test_four_column_last_exchange_within_a_warp(LF):
+    """The column passes synchronise the exchange between their last two
+    register stages (either direction) with __syncwarp (kernels_col4.cu,
+    c4_stage_sync): every slot is owned by threads of one warp in both
+    stages; the earlier exchanges cross warps and keep CTA barriers."""
+    NST = (LF + 3) // 4
+    a, b = _c4_stage_owners(LF, NST - 2), _c4_stage_owners(LF, NST - 1)
+    assert set(a) == set(b) == set(range(4096))
+    assert all(a[k] // 32 == b[k] // 32 for k in a)
+    if NST > 2:
+        c = _c4_stage_owners(LF, NST - 3)
+        assert any(c[k] // 32 != a[k] // 32 for k in a)
+
+
 def test_tile_address_identities():
     """The tile kernel computes its shared-memory addresses from per-thread
     bases and compile-time terms; the identities behind that, for every
