@@ -285,9 +285,9 @@ _KSRC = {
     "k_tile4096": ["kernels_tile.cu", "tile_dev.cuh", "tma.cuh", "tma_host.cu", "modarith.cuh", "kernels_mod.hpp"],
 }
 NCU_TRAFFIC = {
-    "k_colfwd4": (385131264, "52e6bfa917e1237b"),
-    "k_tile4096": (563296256, "ca6914afd827ac5b"),
-    "k_colinv4x3": (304125440, "1718e74ab219e9fd"),
+    "k_colfwd4": (384811520, "ee0c8d47108b47c2"),
+    "k_tile4096": (564259840, "3644a8de0c4ee66d"),
+    "k_colinv4x3": (304274944, "e4db7899ecdb92b8"),
 }
 
 
