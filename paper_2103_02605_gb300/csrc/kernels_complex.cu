@@ -318,13 +318,24 @@ __device__ __forceinline__ void crec_stage0_regs(SideT<T, TW> &sd, int t, T *r)
     }
 }
 
+// The last stage (8 contiguous numbers at 8 t) exchanges numbers with the
+// last register stage only between threads of one warp: the register
+// stage's blocks of 2^(n - d0) numbers are 8 threads', cpos permutes inside
+// 16-number blocks, and an instance's n / 8 threads are whole warps or lie
+// inside one (checked on the CPU for n = 16 .. 4096).  So the barriers on
+// either side of the last stage are warp syncs; the other stages' exchanges
+// cross warps.
+
 // whole product for one instance: forward stages, last stage, recombination
 template <int M, int S, class T, class TW>
 __device__ __forceinline__ void cfwd_all(SideT<T, TW> &sd, int t)
 {
     if constexpr (S < CShape<M>::NST) {
         cfwd_stage<M, S, T, TW>(sd, t);
-        __syncthreads();
+        if constexpr (S == CShape<M>::NST - 1)
+            __syncwarp();   // next: the last stage
+        else
+            __syncthreads();
         cfwd_all<M, S + 1, T, TW>(sd, t);
     }
 }
@@ -345,7 +356,7 @@ __device__ __forceinline__ void cproduct(SideT<T, TW> &sd, int t)
 {
     cfwd_all<M, 0, T, TW>(sd, t);
     cleaf_stage<M, T, TW>(sd, t);
-    __syncthreads();
+    __syncwarp();
     crec_all<M, CShape<M>::NST - 1, T, TW>(sd, t);
 }
 
@@ -360,10 +371,13 @@ __device__ __forceinline__ void cproduct_regs(SideT<T, TW> &sd, int t, T *r, T *
 {
     static_assert(CShape<M>::NST >= 1, "n >= 16");
     cfwd_stage0_regs<M, T, TW>(sd, t, r, x);
-    __syncthreads();
+    if constexpr (CShape<M>::NST == 1)
+        __syncwarp();   // next: the last stage (n <= 64: the instance is inside one warp)
+    else
+        __syncthreads();
     cfwd_all<M, 1, T, TW>(sd, t);
     cleaf_stage<M, T, TW>(sd, t);
-    __syncthreads();
+    __syncwarp();
     crec_all<M, CShape<M>::NST - 1, T, TW, 1>(sd, t);
     crec_stage0_regs<M, T, TW>(sd, t, r);
 }

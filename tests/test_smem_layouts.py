@@ -309,6 +309,39 @@ def _cpos(e):
     return e ^ (((e >> 4) & 7) | (((e >> 6) & 1) << 3))
 
 
+@pytest.mark.parametrize("M", range(4, 13))
+@pytest.mark.parametrize("swz", [True, False])
+def test_complex_leaf_exchange_within_a_warp(M, swz):
+    """The complex-layer kernels (and GF(p^2), Z/(2^K + 1), which keep the
+    plain layout) synchronise the exchanges around their last stage with
+    __syncwarp (kernels_complex.cu): every number the last stage (8
+    contiguous numbers at 8 t) exchanges with the last register stage is
+    held, in both, by threads of one warp; an instance's n / 8 threads are
+    whole warps or lie inside one."""
+    pos = _cpos if swz else (lambda e: e)
+    N, NTI = 1 << M, (1 << M) // 8
+    L = M - 1
+    P = L - 2
+    NST = (P + 2) // 3
+    nl = (lambda s: P - 3 * (NST - 1) if s == 0 else 3)
+    d0 = (lambda s: 0 if s == 0 else (P - 3 * (NST - 1)) + 3 * (s - 1))
+    S = NST - 1
+    NL, D0 = nl(S), d0(S)
+    G, MM, LST, LRB = 8 >> NL, 1 << NL, M - D0 - NL, M - D0
+    own = {}
+    for t in range(NTI):
+        for h in range(G):
+            gg = t + NTI * h
+            blk, off = gg >> LST, gg & ((1 << LST) - 1)
+            for i in range(MM):
+                own[pos((blk << LRB) + off + (i << LST))] = t
+    assert sorted(own) == list(range(N))
+    assert NTI % 32 == 0 or 32 % NTI == 0
+    for t in range(NTI):
+        for i in range(8):
+            assert own[pos(8 * t + i)] // 32 == t // 32
+
+
 def _complex_patterns(M):
     """Every shared-memory access of the complex kernels for n = 2^M, as one
     list of (instance, element) per warp instruction: the loads/stores
